@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the self-gravity field solve on GB300.
+
+One step = one pass of the whole hot path over one disc: ``sg_solve`` on a
+2048 x 4096 log-polar grid (gas, h = 0.05, FP32 FFT path, outputs Phi, g_r
+and g_phi), i.e. the row R2C, the fused column pass and the row C2R with
+epilogue.  The kernel spectra are built once per plan (the paper
+precomputes the kernel for the whole run) and are not part of a step; their
+build time is reported separately.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank solves its own
+independent disc (no data exchange), so the job scales weakly; the time is
+the maximum over ranks.  ``--impl reference`` times the FP64 CPU oracle on
+the same workload on the host cores (rank 0 only).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SG field cells/s and HBM roofline fraction at rel-L2<=1e-5 vs FP64 oracle"
+UNIT = "cells/s"
+L2_FLUSH_BYTES = 256 << 20
+PROFILE = os.path.join(ROOT, "profiles", "cols_2048x4096.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--nr", type=int, default=2048)
+    ap.add_argument("--nphi", type=int, default=4096)
+    ap.add_argument("--bifluid", action="store_true", help="gas + dust (St = 0.1) instead of gas only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_2506_10812_gb300 import inputs
+    if args.bifluid:
+        return inputs.lognormal_bifluid(args.nr, args.nphi, St=0.1, offset=3 + 1000 * rank)
+    return inputs.lognormal_gas(args.nr, args.nphi, offset=2 + 1000 * rank)
+
+
+def config_of(args, d):
+    return {"workload": d.label + f", h_g={d.h_g}" + (f", h_d={d.h_d:.4g}" if d.h_d else "")
+            + ", FFT path, outputs Phi + g_r + g_phi per fluid",
+            "nr": d.nr, "nphi": d.nphi, "r_in": d.r_in, "r_out": d.r_out,
+            "fluids": 2 if d.sigma_d is not None else 1,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "kernel_spectra": "built once per plan, outside the timed steps"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        self.t0 = time.time()
+
+    def mark(self):
+        return time.time()
+
+    def stop(self, t_begin, t_end):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        # samples come every 50 ms from start(); keep those inside the timed window
+        n0 = max(0, int((t_begin - self.t0) / 0.05) - 1)
+        n1 = int((t_end - self.t0) / 0.05) + 2
+        sel = rows[n0:n1] or rows
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in sel for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(s for s, _, _ in sel), "sm_max_mhz": max(m for _, m, _ in sel),
+                "reasons": reasons, "samples": len(sel)}
+
+
+# -------------------------------------------------------------- roofline
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("sg_kernels.cu", "sg_fft.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_10812_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per column-pass launch from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not (m and t) or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+# -------------------------------------------------------------- multi-GPU
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x, world):
+    """Maximum over ranks (identity for one process)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------ CPU oracle
+def time_oracle(d, repeats, sample_note):
+    import oracle
+    g = oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out)
+    plan = oracle.fft64_plan(g, d.h_g, d.h_d if d.sigma_d is not None else None, d.G)
+    times, out = [], None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        out = oracle.fft64_apply(plan, d.sigma_g, d.sigma_d)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return out, {"value": d.cells / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                 "sample": sample_note.format(n=repeats, t=t)}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+    from paper_2506_10812_gb300 import Plan
+    d = workload(args, rank)
+    t0 = time.perf_counter()
+    plan = Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, device=dev)
+    plan_build_ms = (time.perf_counter() - t0) * 1e3
+    sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
+    sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=torch.float32, device=dev)
+    out = plan.solve(sg, sd)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    K, W = args.steps, args.warmup
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    import ctypes
+    for _ in range(W):
+        flush.fill_(1.0)
+        plan.solve(sg, sd, out=out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.1)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_begin = time.time()
+    lib, handle = plan._lib, plan._h
+    for k in range(K):
+        flush.fill_(1.0)
+        e = ev[k]
+        arr = (ctypes.c_void_p * 4)(*[x.cuda_event for x in e[1:5]])
+        lib.sg_set_stage_events(handle, arr)
+        e[0].record()
+        plan.solve(sg, sd, out=out)
+        e[5].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    t_end = time.time()
+    lib.sg_set_stage_events(handle, None)
+    clk = clocks.stop(t_begin, t_end)
+    step_ms = [e[0].elapsed_time(e[5]) for e in ev]
+    stage = {"rows_fwd": [e[1].elapsed_time(e[2]) for e in ev], "cols": [e[2].elapsed_time(e[3]) for e in ev],
+             "rows_inv": [e[3].elapsed_time(e[4]) for e in ev]}
+    total_ms = reduce_max(sum(step_ms), world)
+    ms_per_step = total_ms / K
+    cells_all = d.cells * world
+    value = cells_all / (ms_per_step * 1e-3)
+
+    # ---- roofline of the dominant kernel (the column pass)
+    nsrc = 2 if d.sigma_d is not None else 1
+    ncomp = 3
+    N, nr = d.nphi // 2, d.nr
+    col_bytes = 8 * (nsrc * N * nr + nsrc * nsrc * ncomp * (N + 1) * nr + nsrc * ncomp * N * nr)
+    col_ms = statistics.mean(stage["cols"])
+    peak, peak_kind = measured_peaks()
+    achieved = col_bytes / (col_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_cols (fused column pass)", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+                "peak_source": f"{peak_kind} HBM copy bandwidth", "algorithmic_bytes_per_launch": col_bytes}
+    # whole step against the 3-pass model traffic (60 B/cell gas-only with Phi)
+    step_bytes = col_bytes + 8 * nsrc * N * nr * 2 + 4 * nsrc * d.cells + 8 * nsrc * ncomp * N * nr + 4 * nsrc * ncomp * d.cells
+    step_frac = step_bytes / (ms_per_step * 1e-3) / 1e9 / peak
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    hin_g = torch.from_numpy(d.sigma_g.astype(np.float32)).pin_memory()
+    hin_d = None if d.sigma_d is None else torch.from_numpy(d.sigma_d.astype(np.float32)).pin_memory()
+    hout = {k: torch.empty((d.nr, d.nphi), dtype=torch.float32).pin_memory() for k in out}
+    plan.solve_host(hin_g, hin_d, out=hout)
+    barrier(world)
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        plan.solve_host(hin_g, hin_d, out=hout)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = reduce_max(statistics.mean(e2e_t), world)
+    h2d = 4 * nsrc * d.cells
+    d2h = 4 * len(out) * d.cells
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+              "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+              "dtype": "f32", "data": "synthetic (seeded log-normal disc, no dataset)",
+              "config": config_of(args, d),
+              "roofline": roofline,
+              "step_roofline": {"model_bytes_per_step": step_bytes, "frac": round(step_frac, 4),
+                                "note": "3-pass traffic model over the whole step"},
+              "stages_ms": {k: statistics.mean(v) for k, v in stage.items()},
+              "plan_build_ms": plan_build_ms,
+              "e2e": {"value": cells_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+              "gpu_launches": K * plan.launches_per_solve(),
+              "clocks": clk}
+
+    # ---- oracle: CPU baseline and parity of this very output (rank 0)
+    if rank == 0 and not args.no_cpu_baseline:
+        ref, cpu = time_oracle(d, 3, "median of {n} FP64 FFT-convolution solves of the full disc "
+                                     "(numpy, one core; kernel spectra precomputed), {t:.2f} s each")
+        result["cpu_baseline"] = cpu
+        import oracle
+        got = {k: v.double().cpu().numpy() for k, v in out.items()}
+        result["parity"] = {k: {"rel_l2": oracle.rel_l2(got[k], ref[k]), "rel_max": oracle.rel_max(got[k], ref[k])}
+                            for k in got}
+        result["parity_ok"] = all(v["rel_l2"] <= 1e-5 and v["rel_max"] <= 1e-4 for v in result["parity"].values())
+    plan.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- reference
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    d = workload(args, 0)
+    import oracle
+    g = oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out)
+    plan = oracle.fft64_plan(g, d.h_g, d.h_d if d.sigma_d is not None else None, d.G)
+    W = min(args.warmup, 1)
+    K = max(1, min(args.steps, 8))
+    for _ in range(W):
+        oracle.fft64_apply(plan, d.sigma_g, d.sigma_d)
+    t = []
+    for _ in range(K):
+        t0 = time.perf_counter()
+        oracle.fft64_apply(plan, d.sigma_g, d.sigma_d)
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(t) / K
+    value = d.cells / (ms * 1e-3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded log-normal disc, no dataset)", "config": config_of(args, d),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{K} FP64 FFT-convolution solves of the full disc (numpy, one core; "
+                                   f"kernel spectra precomputed); steps capped at 8 to bound the run"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

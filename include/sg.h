@@ -1,0 +1,175 @@
+/*
+ * sg.h -- C ABI of the GB300 (sm_103a) thin-disc self-gravity library.
+ *
+ * The library computes the 2-D self-gravity potential Phi and the radial and
+ * azimuthal accelerations g_r, g_phi of a Gaussian-stratified thin disc made
+ * of gas and an optional dust fluid, on a log-polar grid, with the exact
+ * Bessel kernel of Rendon Restrepo et al. (2025), "Self-gravity in thin
+ * protoplanetary discs 1":
+ *
+ *   kernel            Sec. 2.2, Eq. "SG force kernel exact"
+ *                     K_ab = (1/sqrt(pi)) H_ab^-2 (d/8) e^X [K1(X) - K0(X)],
+ *                     X = d^2/8, d = s/H_ab,
+ *   scale height      Sec. 2.2, Eq. "mean root square height"
+ *                     H_ab^2 = (H_a(r')^2 + H_b(r)^2) / 2,
+ *   acceleration      Sec. 2.2, Eq. "volume force 2D" divided by Sigma_b:
+ *                     g_b(r) = -G sum_a int Sigma_a(r') K_ab e_s d^2r',
+ *   potential         Sec. 5.6, Eq. "grav. potential 2D":
+ *                     Phi_b(r) = -G sum_a int Sigma_a(r') e^X K0(X) / (2 sqrt(pi) H_ab) d^2r',
+ *   fast method       Sec. 5.2 and App. C: for constant aspect ratios h_a, h_b
+ *                     the sums are convolutions on the log-polar lattice,
+ *                     evaluated by a 2-D FFT with the radial direction
+ *                     zero-padded to 2 nr; the kernel spectra are built once
+ *                     per plan (Sec. 5.2: precomputed for the whole run).
+ *
+ * Discretisation: nr cells log-spaced between the radial EDGES r_in and
+ * r_out, centres r_i = r_in exp((i + 1/2) du), du = ln(r_out/r_in)/nr;
+ * nphi cells, centres phi_j = (j + 1/2) 2 pi / nphi.  Cell mass
+ * Sigma r_i^2 du dphi (midpoint rule).  The self cell is excluded for every
+ * fluid pair.  The paper states no discretisation; this one makes the FFT
+ * convolution and the direct pair sum the same finite sum.
+ *
+ * Memory: every field argument is a caller-owned DEVICE buffer, contiguous
+ * row-major [nr][nphi] (phi fastest), in the plan's dtype (float for SG_F32,
+ * double for SG_F64), unless a function says otherwise.  The plan owns its
+ * kernel spectra and scratch, allocated by sg_plan_create and released by
+ * sg_destroy.  sg_solve / sg_potential / sg_accel allocate nothing, never
+ * synchronise the host, and enqueue their work on `stream` (a cudaStream_t;
+ * NULL is the legacy default stream).  A plan must not be used by two
+ * streams at once (its scratch is shared).
+ *
+ * Errors: arguments are checked on the host before anything is enqueued;
+ * a failed check returns SG_ERR_ARG (or SG_ERR_UNSUPPORTED /
+ * SG_ERR_NOT_FFT_COMPATIBLE) and enqueues nothing.  A CUDA launch error
+ * returns SG_ERR_CUDA.  sg_last_error() gives a one-line description of the
+ * plan's most recent failure.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_plan sg_plan;
+
+typedef enum {
+    SG_OK = 0,
+    SG_ERR_ARG = 1,                /* invalid argument (NULL, size, range)          */
+    SG_ERR_UNSUPPORTED = 2,        /* valid but not implemented (size, dtype combo) */
+    SG_ERR_NOT_FFT_COMPATIBLE = 3, /* FFT method asked with non-constant H          */
+    SG_ERR_CUDA = 4,               /* a CUDA runtime call or launch failed          */
+    SG_ERR_OOM = 5,                /* device allocation failed                      */
+    SG_ERR_NONFINITE = 6,          /* SG_CHECK_FINITE found a NaN/Inf output         */
+    SG_ERR_TIMEOUT = 7             /* reserved                                       */
+} sg_status;
+
+enum { SG_F32 = 0, SG_F64 = 1 };                  /* plan dtype                        */
+enum { SG_METHOD_FFT = 0, SG_METHOD_DIRECT = 1 };  /* App. C convolution / direct sum   */
+/* Ordered fluid pairs, source -> target (Sec. 2.2 names the four
+ * combinations; pointwise K_gd = K_dg, but the lattice tables differ). */
+enum { SG_PAIR_GG = 0, SG_PAIR_GD = 1, SG_PAIR_DG = 2, SG_PAIR_DD = 3 };
+enum { SG_COMP_PHI = 0, SG_COMP_R = 1, SG_COMP_AZ = 2 };
+
+#define SG_CHECK_FINITE 2u  /* flag: record NaN/Inf outputs, reported by sg_sync */
+
+typedef struct {
+    int32_t nr, nphi;        /* cells.  FFT method: powers of two, 8 <= nr <= 4096,
+                                32 <= nphi <= 8192.  DIRECT: nr >= 1, nphi >= 1    */
+    double r_in, r_out;      /* radial cell edges, 0 < r_in < r_out                 */
+    double h_g, h_d;         /* aspect ratios H^sg/r of gas and dust (> 0);
+                                h_d <= 0 means a gas-only disc                      */
+    const void *H_g_field;   /* DIRECT only, optional: device [nr][nphi] H_g^sg(r,phi)
+                                in the plan dtype (copied at create); NULL = h_g r  */
+    const void *H_d_field;   /* DIRECT only, optional, as above for dust            */
+    double G;                /* gravitational constant (the paper's tests use 1)   */
+    int32_t dtype;           /* SG_F32 or SG_F64                                    */
+    int32_t method;          /* SG_METHOD_FFT or SG_METHOD_DIRECT                   */
+    uint32_t flags;          /* SG_CHECK_FINITE                                     */
+} sg_params;
+
+/* Create a plan: validate `p`, allocate the plan's device memory and, for the
+ * FFT method, build the kernel spectra of every fluid pair (Sec. 5.2: the
+ * kernel depends on the grid and the aspect ratios only, so it is computed
+ * once).  The build runs on `stream`; the call synchronises `stream` before
+ * returning.  On success *out holds the plan (owned by the caller, release
+ * with sg_destroy); on failure *out is NULL and nothing stays allocated.   */
+sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream);
+
+/* Write the real-space lattice kernel of one ordered fluid pair and one
+ * component (App. C), K_c(Delta_i du, Delta_j dphi) for Delta_i in
+ * [-nr, nr) stored circularly in 2 nr rows (row k <-> Delta_i = k for
+ * k < nr, k - 2 nr otherwise; row nr, the lag never used, is 0) and Delta_j
+ * in [0, nphi):
+ *     COMP_PHI: e^{-3D/2} e^X K0(X) / (2 sqrt(pi) h_ab)
+ *     COMP_R  : e^{-3D/2} (e^D - cos psi) D(X) / (8 sqrt(pi) h_ab^3)
+ *     COMP_AZ : e^{-3D/2} sin psi D(X) / (8 sqrt(pi) h_ab^3)
+ * with D = Delta_i du, psi = Delta_j dphi, h_ab^2 = (h_a^2 e^-D + h_b^2 e^D)/2,
+ * d^2 = 4 [sinh^2(D/2) + sin^2(psi/2)] / h_ab^2, X = d^2/8, D(X) =
+ * e^X [K1(X) - K0(X)] and the self entry (0, 0) = 0.  `out_dev` is a device
+ * buffer of 2 nr * nphi elements of the plan dtype.  FFT method only
+ * (SG_ERR_UNSUPPORTED otherwise); a dust pair needs a bi-fluid plan.
+ * Asynchronous on `stream`.                                                */
+sg_status sg_kernel_table(sg_plan *plan, int pair, int comp, void *out_dev, void *stream);
+
+/* Potential of each target fluid, Phi_b = sum over source fluids a of
+ * Phi^{ab} (Sec. 5.6, Eq. "grav. potential 2D").  sigma_g: Sigma_g [nr][nphi];
+ * sigma_d: Sigma_d, required for a bi-fluid plan and ignored otherwise.
+ * phi_g / phi_d: outputs for the gas / dust targets; either may be NULL to
+ * skip it (phi_d is ignored for a gas-only plan).  Asynchronous.           */
+sg_status sg_potential(sg_plan *plan, const void *sigma_g, const void *sigma_d,
+                       void *phi_g, void *phi_d, void *stream);
+
+/* Accelerations g_r, g_phi (force per unit mass, Sec. 2.2 Eq. "volume force
+ * 2D" divided by Sigma_b) of each target fluid, summed over the source
+ * fluids.  Any output pointer may be NULL to skip it.  Asynchronous.       */
+sg_status sg_accel(sg_plan *plan, const void *sigma_g, const void *sigma_d,
+                   void *gr_g, void *gphi_g, void *gr_d, void *gphi_d, void *stream);
+
+/* sg_potential and sg_accel fused: one forward transform of each source
+ * serves every requested output.  Any output pointer may be NULL.          */
+sg_status sg_solve(sg_plan *plan, const void *sigma_g, const void *sigma_d,
+                   void *phi_g, void *gr_g, void *gphi_g,
+                   void *phi_d, void *gr_d, void *gphi_d, void *stream);
+
+/* sg_solve with HOST buffers: inputs and outputs are host memory (pinned
+ * memory gives full copy bandwidth).  The call copies the inputs to
+ * plan-owned device buffers, solves, copies the requested outputs back and
+ * synchronises `stream` before returning.  The first call allocates the
+ * plan's staging buffers.                                                  */
+sg_status sg_solve_host(sg_plan *plan, const void *sigma_g, const void *sigma_d,
+                        void *phi_g, void *gr_g, void *gphi_g,
+                        void *phi_d, void *gr_d, void *gphi_d, void *stream);
+
+/* Synchronise `stream` and report the plan's finite check: SG_ERR_NONFINITE
+ * if an output written since the previous sg_sync held a NaN or Inf (plans
+ * created with SG_CHECK_FINITE), SG_ERR_CUDA on an asynchronous CUDA error,
+ * SG_OK otherwise.  Clears the flag.                                       */
+sg_status sg_sync(sg_plan *plan, void *stream);
+
+/* Number of kernel launches one sg_solve call enqueues for the outputs
+ * selected by `outmask` (bit 3 b + c for target b in {gas, dust} and
+ * component c in SG_COMP_*).                                               */
+int32_t sg_launches_per_solve(const sg_plan *plan, uint32_t outmask);
+
+/* Stage timing: with `events` pointing at four cudaEvent_t handles (created
+ * by the caller), every following solve records events[0] before its first
+ * launch, events[1] after the row transforms, events[2] after the column
+ * pass and events[3] after the last launch, on the solve's stream (direct
+ * method: events[1..3] after the pair sum).  NULL stops the recording.    */
+sg_status sg_set_stage_events(sg_plan *plan, void *const *events);
+
+/* Release a plan and all its device memory (NULL is a no-op).  Synchronises
+ * the device before freeing.                                               */
+void sg_destroy(sg_plan *plan);
+
+const char *sg_status_string(sg_status s);
+const char *sg_last_error(const sg_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

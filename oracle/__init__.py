@@ -272,33 +272,51 @@ def conv_tables(grid, h_a, h_b):
     return KP, Kr, Kp
 
 
-def fft64(grid, sigma_g, sigma_d=None, h_g=0.05, h_d=None, G=1.0):
-    """FP64 zero-padded FFT convolution (Sec. 5.2: log grid, radial padding
-    to 2 nr; App. C kernels; bi-fluid sums over sources as in Sec. 5.2's
+def fft64_plan(grid, h_g=0.05, h_d=None, G=1.0):
+    """Kernel spectra of every ordered (source, target) pair (Sec. 5.2: the
+    kernel depends only on the grid and the aspect ratios, so it is
+    transformed once)."""
+    fl = [("g", h_g)] + ([("d", h_d)] if h_d is not None and h_d > 0 else [])
+    spectra = {}
+    for sname, ha in fl:
+        for tname, hb in fl:
+            spectra[(sname, tname)] = [np.fft.rfft2(t) for t in conv_tables(grid, ha, hb)]
+    return {"grid": grid, "fluids": [f for f, _ in fl], "G": G, "spectra": spectra}
+
+
+def fft64_apply(plan, sigma_g, sigma_d=None):
+    """FP64 zero-padded FFT convolution (Sec. 5.2: log grid, radial padding to
+    2 nr; App. C kernels; bi-fluid sums over sources as in Sec. 5.2's
     multi-fluid equations, with one table per ordered pair)."""
+    grid = plan["grid"]
     nr, nphi = grid.nr, grid.nphi
-    srcs = [("g", _c64(sigma_g), h_g)]
-    if sigma_d is not None:
-        srcs.append(("d", _c64(sigma_d), h_d))
+    srcs = {"g": _c64(sigma_g)}
+    if "d" in plan["fluids"]:
+        srcs["d"] = _c64(sigma_d)
     spec = {}
-    for name, sig, _ in srcs:
+    for name, sig in srcs.items():
         pad = np.zeros((2 * nr, nphi))
         pad[:nr] = sig
         spec[name] = np.fft.rfft2(pad)
     out = {}
     r = grid.r[:, None]
-    scale = -G * grid.du * grid.dphi
-    for tname, _, hb in srcs:
+    scale = -plan["G"] * grid.du * grid.dphi
+    for tname in srcs:
         acc = [0.0, 0.0, 0.0]
-        for sname, _, ha in srcs:
-            tabs = conv_tables(grid, ha, hb)
+        for sname in srcs:
+            tabs = plan["spectra"][(sname, tname)]
             for c in range(3):
-                acc[c] = acc[c] + spec[sname] * np.fft.rfft2(tabs[c])
+                acc[c] = acc[c] + spec[sname] * tabs[c]
         res = [np.fft.irfft2(a, s=(2 * nr, nphi))[:nr] * scale for a in acc]
         out["phi_" + tname] = res[0] * r
         out["gr_" + tname] = res[1]
         out["gphi_" + tname] = res[2]
     return out
+
+
+def fft64(grid, sigma_g, sigma_d=None, h_g=0.05, h_d=None, G=1.0):
+    """``fft64_apply(fft64_plan(...), ...)`` in one call."""
+    return fft64_apply(fft64_plan(grid, h_g, h_d if sigma_d is not None else None, G), sigma_g, sigma_d)
 
 
 # --------------------------------------------------------------------------

@@ -1,0 +1,94 @@
+"""ctypes declarations of the C ABI in ``include/sg.h`` (``libsg.so``).
+
+Loading fails loudly when the library has not been built: there is no CPU
+fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsg.so")
+
+SG_OK, SG_ERR_ARG, SG_ERR_UNSUPPORTED, SG_ERR_NOT_FFT_COMPATIBLE, SG_ERR_CUDA, SG_ERR_OOM, \
+    SG_ERR_NONFINITE, SG_ERR_TIMEOUT = range(8)
+SG_F32, SG_F64 = 0, 1
+SG_METHOD_FFT, SG_METHOD_DIRECT = 0, 1
+SG_PAIR_GG, SG_PAIR_GD, SG_PAIR_DG, SG_PAIR_DD = 0, 1, 2, 3
+SG_COMP_PHI, SG_COMP_R, SG_COMP_AZ = 0, 1, 2
+SG_CHECK_FINITE = 2
+
+# Every symbol include/sg.h declares (checked by the ABI test).
+EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
+           "sg_solve_host", "sg_sync", "sg_set_stage_events", "sg_launches_per_solve", "sg_destroy", "sg_status_string",
+           "sg_last_error")
+
+
+class SgParams(ctypes.Structure):
+    _fields_ = [("nr", ctypes.c_int32), ("nphi", ctypes.c_int32),
+                ("r_in", ctypes.c_double), ("r_out", ctypes.c_double),
+                ("h_g", ctypes.c_double), ("h_d", ctypes.c_double),
+                ("H_g_field", ctypes.c_void_p), ("H_d_field", ctypes.c_void_p),
+                ("G", ctypes.c_double), ("dtype", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class SgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libsg.so`` (built in-tree by ``paper_2506_10812_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -m paper_2506_10812_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32
+    st = ctypes.c_int
+    lib.sg_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(SgParams), vp]
+    lib.sg_plan_create.restype = st
+    lib.sg_kernel_table.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.sg_kernel_table.restype = st
+    lib.sg_potential.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.sg_potential.restype = st
+    lib.sg_accel.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.sg_accel.restype = st
+    lib.sg_solve.argtypes = [vp] * 10
+    lib.sg_solve.restype = st
+    lib.sg_solve_host.argtypes = [vp] * 10
+    lib.sg_solve_host.restype = st
+    lib.sg_sync.argtypes = [vp, vp]
+    lib.sg_sync.restype = st
+    lib.sg_set_stage_events.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.sg_set_stage_events.restype = st
+    lib.sg_launches_per_solve.argtypes = [vp, u32]
+    lib.sg_launches_per_solve.restype = i32
+    lib.sg_destroy.argtypes = [vp]
+    lib.sg_destroy.restype = None
+    lib.sg_status_string.argtypes = [st]
+    lib.sg_status_string.restype = ctypes.c_char_p
+    lib.sg_last_error.argtypes = [vp]
+    lib.sg_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def check(status: int, plan_handle=None, what: str = "sg call") -> None:
+    if status == SG_OK:
+        return
+    lib = load()
+    msg = lib.sg_status_string(status).decode()
+    if plan_handle:
+        detail = lib.sg_last_error(plan_handle).decode()
+        if detail:
+            msg = f"{msg}: {detail}"
+    raise SgError(status, f"{what}: {msg}")

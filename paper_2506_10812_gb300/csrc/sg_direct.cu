@@ -1,0 +1,159 @@
+// Direct O(N^2) pair sum with position-dependent scale heights (Sec. 2.2):
+//     g_b(r) = -G sum_a sum_{cells r' != r} m_a(r') K_ab(r, r') e_s,
+//     Phi_b(r) = -G sum_a sum_{cells r' != r} m_a(r') e^X K0(X) / (2 sqrt(pi) H_ab),
+// m_a = Sigma_a r'^2 du dphi, H_ab^2 = (H_a(r')^2 + H_b(r)^2) / 2 (Eq. "mean
+// root square height"), X = s^2 / (8 H_ab^2).  This is the parity path of
+// the library and the only one valid for non-constant H/r.
+//
+// The pair geometry is taken from the integer index differences
+// (di, dj) = (i - i', j - j'), with Delta = di du and psi = dj dphi:
+//     s^2            = 4 r r' [sinh^2(Delta/2) + sin^2(psi/2)],
+//     e_r . (r - r') = r' [expm1(Delta) + 2 sin^2(psi/2)],
+//     e_phi . (r - r') = r' sin psi,
+// using per-lag tables built in FP64, so FP32 keeps full relative precision
+// for the nearest neighbours (no cancellation in r - r').
+#include <math.h>
+
+#include "sg_bessel.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+template <typename R> struct pair_of;
+template <> struct pair_of<float> { using type = float2; };
+template <> struct pair_of<double> { using type = double2; };
+
+template <typename R> struct Acc {
+    R s = 0, c = 0;
+    __device__ __forceinline__ void add(R v)   // Kahan-compensated sum
+    {
+        R y = v - c;
+        R t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ void k0e_D_any(R x, const BesselWeights &bw, R &k0e, R &D);
+template <>
+__device__ __forceinline__ void k0e_D_any<double>(double x, const BesselWeights &bw, double &k0e, double &D)
+{
+    k0e_D_f64(x, bw, k0e, D);
+}
+template <>
+__device__ __forceinline__ void k0e_D_any<float>(float x, const BesselWeights &bw, float &k0e, float &D)
+{
+    if (x < 1.0f) {   // log singularity region: FP64
+        double a, b;
+        k0e_D_f64((double)x, bw, a, b);
+        k0e = (float)a;
+        D = (float)b;
+    } else {
+        k0e_D_f32(x, bw, k0e, D);
+    }
+}
+
+constexpr int DT = 256;   // targets per CTA and sources per shared-memory tile
+
+template <typename R>
+__global__ void __launch_bounds__(DT)
+k_direct(int nr, int nphi, R G, const R *__restrict__ sig_g, const R *__restrict__ sig_d,
+         const R *__restrict__ Hg, const R *__restrict__ Hd, R h_g, R h_d, int tgt, R *phi, R *gr,
+         R *gphi, const typename pair_of<R>::type *__restrict__ geo_i,
+         const typename pair_of<R>::type *__restrict__ geo_j, const R *__restrict__ rcen, R dudphi,
+         unsigned int *flag)
+{
+    using P2 = typename pair_of<R>::type;
+    __shared__ BesselWeights bw;
+    __shared__ R s_r[DT], s_m[DT], s_H2[DT];
+    __shared__ int s_i[DT], s_j[DT];
+    bessel_weights_init(bw);
+    const int ncell = nr * nphi;
+    const int tid = blockIdx.x * DT + threadIdx.x;
+    const bool valid = tid < ncell;
+    const int i = valid ? tid / nphi : 0;
+    const int j = valid ? tid - i * nphi : 0;
+    const R r = rcen[i];
+    const R *Hb_f = tgt == 0 ? Hg : Hd;
+    const R hb = tgt == 0 ? h_g : h_d;
+    const R Hb = valid ? (Hb_f ? Hb_f[tid] : hb * r) : (R)1;
+    const R Hb2 = Hb * Hb;
+    const R c_force = (R)(0.125 * 0.56418958354775628695);   // 1 / (8 sqrt(pi))
+    const R c_pot = (R)(0.5 * 0.56418958354775628695);       // 1 / (2 sqrt(pi))
+    Acc<R> agr, agp, aph;
+    const int nsrc_fluids = sig_d ? 2 : 1;
+    for (int a = 0; a < nsrc_fluids; ++a) {
+        const R *sig = a == 0 ? sig_g : sig_d;
+        const R *Ha_f = a == 0 ? Hg : Hd;
+        const R ha = a == 0 ? h_g : h_d;
+        for (int s0 = 0; s0 < ncell; s0 += DT) {
+            __syncthreads();
+            const int src = s0 + threadIdx.x;
+            if (src < ncell) {
+                const int ii = src / nphi, jj = src - (src / nphi) * nphi;
+                const R rr = rcen[ii];
+                const R Ha = Ha_f ? Ha_f[src] : ha * rr;
+                s_r[threadIdx.x] = rr;
+                s_m[threadIdx.x] = G * sig[src] * rr * rr * dudphi;
+                s_H2[threadIdx.x] = Ha * Ha;
+                s_i[threadIdx.x] = ii;
+                s_j[threadIdx.x] = jj;
+            }
+            __syncthreads();
+            const int cnt = min(DT, ncell - s0);
+            if (!valid) continue;
+            for (int q = 0; q < cnt; ++q) {
+                if (s0 + q == tid) continue;                 // self cell excluded
+                const int di = i - s_i[q];
+                int dj = j - s_j[q];
+                if (dj < 0) dj += nphi;
+                const P2 gi = geo_i[di + nr - 1];            // (sinh^2(D/2), expm1(D))
+                const P2 gj = geo_j[dj];                     // (sin^2(psi/2), sin psi)
+                const R rr = s_r[q];
+                const R s2 = (R)4 * r * rr * (gi.x + gj.x);
+                const R H2 = (R)0.5 * (s_H2[q] + Hb2);
+                const R X = s2 / ((R)8 * H2);
+                R k0e, D;
+                k0e_D_any<R>(X, bw, k0e, D);
+                const R invH = (R)1 / sqrt(H2);
+                const R f = -s_m[q] * D * c_force * invH * invH * invH;   // -G m K / s
+                agr.add(f * rr * (gi.y + (R)2 * gj.x));
+                agp.add(f * rr * gj.y);
+                aph.add(-s_m[q] * k0e * c_pot * invH);
+            }
+        }
+    }
+    if (!valid) return;
+    if (phi) phi[tid] = aph.s;
+    if (gr) gr[tid] = agr.s;
+    if (gphi) gphi[tid] = agp.s;
+    if (flag && !(isfinite(aph.s) && isfinite(agr.s) && isfinite(agp.s))) atomicOr(flag, 1u);
+}
+
+template <typename R>
+cudaError_t launch_direct(int nr, int nphi, double r_in, double du, double G, const R *sig_g,
+                          const R *sig_d, const R *Hg, const R *Hd, double h_g, double h_d, int tgt,
+                          R *phi, R *gr, R *gphi, const R *geo_i, const R *geo_j, const R *rcen,
+                          unsigned int *flag, cudaStream_t s)
+{
+    (void)r_in;
+    using P2 = typename pair_of<R>::type;
+    const int ncell = nr * nphi;
+    const double dphi = 2.0 * M_PI / nphi;
+    k_direct<R><<<(ncell + DT - 1) / DT, DT, 0, s>>>(
+        nr, nphi, (R)G, sig_g, sig_d, Hg, Hd, (R)h_g, (R)h_d, tgt, phi, gr, gphi, (const P2 *)geo_i,
+        (const P2 *)geo_j, rcen, (R)(du * dphi), flag);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_direct<float>(int, int, double, double, double, const float *, const float *,
+                                          const float *, const float *, double, double, int, float *,
+                                          float *, float *, const float *, const float *, const float *,
+                                          unsigned int *, cudaStream_t);
+template cudaError_t launch_direct<double>(int, int, double, double, double, const double *, const double *,
+                                           const double *, const double *, double, double, int, double *,
+                                           double *, double *, const double *, const double *,
+                                           const double *, unsigned int *, cudaStream_t);
+
+}  // namespace sg

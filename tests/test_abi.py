@@ -1,0 +1,94 @@
+"""The C ABI library builds, loads and exports every function include/sg.h
+declares; host-side argument checks reject bad plans before any CUDA call.
+(No compute call here: this file runs without a GPU.)"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2506_10812_gb300 import _native as N
+from paper_2506_10812_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return N.load()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "sg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sg_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_five_paper_entry_points():
+    names = declared_functions()
+    for f in ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_destroy"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert set(names) == set(N.EXPORTS)
+    for f in names:
+        assert hasattr(lib, f), f
+
+
+def test_library_is_built_for_sm103a():
+    # the build passes exactly one -gencode, for sm_103a
+    assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert os.path.exists(B.LIB_PATH)
+
+
+def _params(**kw):
+    p = N.SgParams()
+    p.nr, p.nphi, p.r_in, p.r_out, p.h_g, p.h_d, p.G = 64, 128, 0.2, 2.5, 0.05, 0.0, 1.0
+    p.dtype, p.method = N.SG_F32, N.SG_METHOD_FFT
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(r_in=2.0, r_out=1.0), N.SG_ERR_ARG),
+    (dict(r_in=0.0), N.SG_ERR_ARG),
+    (dict(nr=0), N.SG_ERR_ARG),
+    (dict(h_g=0.0), N.SG_ERR_ARG),
+    (dict(h_g=float("nan")), N.SG_ERR_ARG),
+    (dict(G=float("inf")), N.SG_ERR_ARG),
+    (dict(dtype=7), N.SG_ERR_ARG),
+    (dict(method=5), N.SG_ERR_ARG),
+    (dict(nr=48), N.SG_ERR_UNSUPPORTED),
+    (dict(nphi=16), N.SG_ERR_UNSUPPORTED),
+    (dict(nr=8192), N.SG_ERR_UNSUPPORTED),
+    (dict(H_g_field=1234), N.SG_ERR_NOT_FFT_COMPATIBLE),
+])
+def test_plan_argument_checks(lib, kw, status):
+    h = ctypes.c_void_p(99)
+    p = _params(**kw)
+    st = lib.sg_plan_create(ctypes.byref(h), ctypes.byref(p), None)
+    assert st == status
+    assert not h.value
+
+
+def test_null_arguments(lib):
+    assert lib.sg_plan_create(None, None, None) == N.SG_ERR_ARG
+    h = ctypes.c_void_p()
+    assert lib.sg_plan_create(ctypes.byref(h), None, None) == N.SG_ERR_ARG
+    assert lib.sg_solve(None, *([None] * 9)) == N.SG_ERR_ARG
+    assert lib.sg_potential(None, None, None, None, None, None) == N.SG_ERR_ARG
+    assert lib.sg_accel(None, *([None] * 7)) == N.SG_ERR_ARG
+    assert lib.sg_kernel_table(None, 0, 0, None, None) == N.SG_ERR_ARG
+    assert lib.sg_launches_per_solve(None, 7) == 0
+    lib.sg_destroy(None)
+    assert lib.sg_last_error(None) == b""
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.sg_status_string(s)
+    assert lib.sg_status_string(N.SG_OK) == b"ok"

@@ -1,0 +1,264 @@
+"""GPU parity: every path of libsg.so against the FP64 CPU oracle, element by
+element, on seeded synthetic discs.
+
+Tolerances: FP64 paths agree with the oracle to 1e-12 (the FFT and the direct
+sum are the same finite sum); FP32 paths meet rel-L2 <= 1e-5 and
+max |x - ref| / max |ref| <= 1e-4 per output field.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_10812_gb300 import _native as N
+from paper_2506_10812_gb300 import build as B
+from paper_2506_10812_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = (1e-5, 1e-4)
+TOL64 = (1e-12, 1e-12)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    B.build()
+    N.load()
+    oracle.build()
+
+
+def P():
+    from paper_2506_10812_gb300 import Plan
+    return Plan
+
+
+def grid(d):
+    return oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out)
+
+
+def gpu_solve(d, dtype=torch.float32, method="fft", H_g=None, H_d=None, outputs=("phi", "gr", "gphi")):
+    dev = torch.device("cuda:0")
+    Hg = None if H_g is None else torch.tensor(H_g, dtype=dtype, device=dev)
+    Hd = None if H_d is None else torch.tensor(H_d, dtype=dtype, device=dev)
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, dtype=dtype, method=method,
+             H_g=Hg, H_d=Hd) as plan:
+        sg = torch.tensor(d.sigma_g, dtype=dtype, device=dev)
+        sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=dtype, device=dev)
+        out = plan.solve(sg, sd, outputs=outputs)
+        torch.cuda.synchronize()
+        return {k: v.double().cpu().numpy() for k, v in out.items()}
+
+
+def assert_close(out, ref, tol, label=""):
+    for k, v in out.items():
+        e2, em = oracle.rel_l2(v, ref[k]), oracle.rel_max(v, ref[k])
+        assert e2 <= tol[0] and em <= tol[1], f"{label} {k}: rel-L2 {e2:.3e} max {em:.3e}"
+
+
+# ---------------------------------------------------------- kernel tables
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-13), (torch.float32, 1e-6)])
+def test_kernel_tables_vs_oracle(dtype, tol):
+    """App. C lattice kernels, all four ordered pairs and three components,
+    entry by entry (the dust-dust table with St = 1 is the most peaked)."""
+    d = inputs.spiral_bifluid(St=1.0, nr=64, nphi=128)
+    g = grid(d)
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, dtype=dtype) as plan:
+        for pair, (ha, hb) in enumerate([(d.h_g, d.h_g), (d.h_g, d.h_d), (d.h_d, d.h_g), (d.h_d, d.h_d)]):
+            ref = oracle.conv_tables(g, ha, hb)
+            for comp in range(3):
+                got = plan.kernel_table(pair, comp).double().cpu().numpy()
+                r = ref[comp]
+                err = np.abs(got - r) / (np.abs(r) + 1e-300)
+                err[r == 0] = np.abs(got[r == 0])
+                assert err.max() <= tol, (pair, comp, err.max())
+
+
+# --------------------------------------------------- small grids, FP64
+def test_fft_fp64_equals_direct_definition():
+    d = inputs.small_gas()
+    ref = oracle.direct(grid(d), d.sigma_g, h_g=d.h_g, G=d.G)
+    assert_close(gpu_solve(d, torch.float64), ref, TOL64, "fft64")
+
+
+def test_direct_fp64_equals_oracle():
+    d = inputs.small_gas()
+    ref = oracle.direct(grid(d), d.sigma_g, h_g=d.h_g, G=d.G)
+    assert_close(gpu_solve(d, torch.float64, method="direct"), ref, TOL64, "direct64")
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+def test_direct_general_scale_heights(dtype, tol):
+    """Position-dependent H_g, H_d (the case the FFT cannot do), two fluids."""
+    d = inputs.ragged_noise(24, 48, bifluid=True)
+    rng = np.random.default_rng(17)
+    R, _ = grid(d).mesh()
+    Hg = R * rng.uniform(0.03, 0.1, R.shape)
+    Hd = R * rng.uniform(0.002, 0.02, R.shape)
+    ref = oracle.direct(grid(d), d.sigma_g, d.sigma_d, H_g=Hg, H_d=Hd, G=d.G)
+    assert_close(gpu_solve(d, dtype, method="direct", H_g=Hg, H_d=Hd), ref, tol, "directH")
+
+
+def test_fft_fp32_small_gas():
+    d = inputs.small_gas()
+    ref = oracle.direct(grid(d), d.sigma_g, h_g=d.h_g, G=d.G)
+    assert_close(gpu_solve(d), ref, TOL32, "fft32")
+
+
+@pytest.mark.parametrize("St", [0.01, 0.1, 1.0])
+def test_bifluid_spiral_fp32(St):
+    d = inputs.spiral_bifluid(St=St)
+    ref = oracle.fft64(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G)
+    assert_close(gpu_solve(d), ref, TOL32, f"St={St}")
+
+
+def test_bifluid_spiral_fp64():
+    d = inputs.spiral_bifluid(St=1.0, nr=128, nphi=256)
+    ref = oracle.fft64(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G)
+    assert_close(gpu_solve(d, torch.float64), ref, TOL64, "bifluid64")
+
+
+@pytest.mark.parametrize("nr,nphi,bif,dtype", [
+    (8, 32, False, torch.float32), (8, 32, True, torch.float64), (16, 64, True, torch.float32),
+    (32, 32, False, torch.float64), (512, 32, True, torch.float32), (16, 1024, False, torch.float32),
+    (4096, 32, False, torch.float32), (8, 8192, True, torch.float32), (64, 2048, False, torch.float64),
+    (128, 128, True, torch.float32)])
+def test_fft_edge_sizes(nr, nphi, bif, dtype):
+    """Smallest and largest supported extents, ragged aspect, each final
+    Stockham radix (2, 4, 8, 16) in both the row and the column transforms."""
+    d = inputs.ragged_noise(nr, nphi, bifluid=bif)
+    ref = oracle.fft64(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G)
+    tol = TOL64 if dtype == torch.float64 else TOL32
+    assert_close(gpu_solve(d, dtype), ref, tol, f"{nr}x{nphi}")
+
+
+# ----------------------------------------------------------- full sizes
+@pytest.mark.parametrize("nr,nphi", [(1024, 2048), (2048, 4096)])
+def test_lognormal_full_size(nr, nphi):
+    """The workload bench.py times (FP32, gas, Phi + g_r + g_phi, one
+    sg_solve), full field against the FP64 FFT oracle and sampled cells
+    against the direct-sum definition."""
+    d = inputs.lognormal_gas(nr, nphi)
+    out = gpu_solve(d)
+    g = grid(d)
+    ref = oracle.fft64(g, d.sigma_g, h_g=d.h_g, G=d.G)
+    assert_close(out, ref, TOL32, f"{nr}x{nphi}")
+    rng = np.random.default_rng(123)
+    idx = np.concatenate([[0, nr * nphi - 1, (nr // 2) * nphi], rng.integers(0, nr * nphi, 13)])
+    samp = oracle.direct(g, d.sigma_g, h_g=d.h_g, G=d.G, targets=idx)
+    for k in ("phi_g", "gr_g", "gphi_g"):
+        got = out[k].ravel()[idx]
+        assert np.abs(got - samp[k]).max() <= TOL32[1] * np.abs(ref[k]).max(), k
+        assert np.abs(ref[k].ravel()[idx] - samp[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
+
+
+def test_lognormal_bifluid_large():
+    d = inputs.lognormal_bifluid(512, 1024, St=1.0)
+    ref = oracle.fft64(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G)
+    assert_close(gpu_solve(d), ref, TOL32, "bif512")
+
+
+# ------------------------------------------------------------ properties
+def test_momentum_conservation_fp32():
+    """Sec. 2.2: pairwise-symmetric forces, so the total force vanishes."""
+    d = inputs.spiral_bifluid(St=0.1)
+    out = gpu_solve(d)
+    R, Pm = grid(d).mesh()
+    g = grid(d)
+    Fx = Fy = 0.0
+    scale = 0.0
+    for f, sig in (("g", d.sigma_g), ("d", d.sigma_d)):
+        m = sig * R * R * g.du * g.dphi
+        gx = out["gr_" + f] * np.cos(Pm) - out["gphi_" + f] * np.sin(Pm)
+        gy = out["gr_" + f] * np.sin(Pm) + out["gphi_" + f] * np.cos(Pm)
+        Fx += (m * gx).sum()
+        Fy += (m * gy).sum()
+        scale += np.abs(m * out["gr_" + f]).sum()
+    assert abs(Fx) / scale < 1e-5 and abs(Fy) / scale < 1e-5
+
+
+def test_axisymmetric_and_zero_inputs():
+    d = inputs.small_gas()
+    R, _ = grid(d).mesh()
+    d.sigma_g = 1.0 / R
+    out = gpu_solve(d)
+    assert np.abs(out["gphi_g"]).max() <= 1e-6 * np.abs(out["gr_g"]).max()
+    assert np.abs(out["gr_g"] - out["gr_g"][:, :1]).max() <= 1e-6 * np.abs(out["gr_g"]).max()
+    d.sigma_g = np.zeros_like(R)
+    out = gpu_solve(d)
+    assert all(np.all(v == 0) for v in out.values())
+
+
+# --------------------------------------------------------- API variants
+def test_potential_accel_host_and_graph_agree_with_solve():
+    d = inputs.spiral_bifluid(St=0.1, nr=128, nphi=256)
+    dev = torch.device("cuda:0")
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G) as plan:
+        sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
+        sd = torch.tensor(d.sigma_d, dtype=torch.float32, device=dev)
+        full = plan.solve(sg, sd)
+        pot = plan.potential(sg, sd)
+        acc = plan.accel(sg, sd)
+        host = plan.solve_host(d.sigma_g.astype(np.float32), d.sigma_d.astype(np.float32))
+        # CUDA-graph capture of sg_solve (no allocation or host sync inside)
+        outb = {k: torch.empty_like(v) for k, v in full.items()}
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            plan.solve(sg, sd, out=outb)
+        torch.cuda.current_stream().wait_stream(s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.solve(sg, sd, out=outb)
+        for v in outb.values():
+            v.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert plan.launches_per_solve() == 3
+    for k, v in full.items():
+        ref = v.cpu()
+        if k.startswith("phi"):
+            assert torch.equal(pot[k].cpu(), ref), k
+        else:
+            assert torch.equal(acc[k].cpu(), ref), k
+        assert np.array_equal(host[k], ref.numpy()), k
+        assert torch.equal(outb[k].cpu(), ref), k
+
+
+def test_G_and_radial_scale():
+    """Linearity in G (the table scale) and radial scale invariance (App. C):
+    edges x2 leave g unchanged and double Phi."""
+    d = inputs.small_gas()
+    a = gpu_solve(d, torch.float64)
+    d2 = inputs.small_gas(G=2.0, r_in=0.4, r_out=5.0)
+    d2.sigma_g = d.sigma_g.copy()
+    b = gpu_solve(d2, torch.float64)
+    for k in a:
+        f = 4.0 if k.startswith("phi") else 2.0
+        assert np.abs(b[k] - f * a[k]).max() <= 1e-13 * np.abs(a[k]).max(), k
+
+
+def test_errors_and_finite_check():
+    dev = torch.device("cuda:0")
+    Plan = P()
+    with pytest.raises(N.SgError) as e:
+        Plan(48, 128, 0.2, 2.5, 0.05)
+    assert e.value.status == N.SG_ERR_UNSUPPORTED
+    Hg = torch.full((64, 128), 0.01, device=dev)
+    with pytest.raises(N.SgError) as e:
+        Plan(64, 128, 0.2, 2.5, 0.05, H_g=Hg)
+    assert e.value.status == N.SG_ERR_NOT_FFT_COMPATIBLE
+    with Plan(64, 128, 0.2, 2.5, 0.05, check_finite=True) as plan:
+        x = torch.ones((64, 128), device=dev)
+        with pytest.raises(ValueError):
+            plan.solve(x.double())
+        with pytest.raises(ValueError):
+            plan.solve(x[:, :64])
+        plan.solve(x)
+        plan.sync()
+        x[3, 5] = float("nan")
+        plan.solve(x)
+        with pytest.raises(N.SgError) as e:
+            plan.sync()
+        assert e.value.status == N.SG_ERR_NONFINITE
+        plan.solve(torch.ones((64, 128), device=dev))
+        plan.sync()                       # flag cleared
