@@ -186,7 +186,14 @@ def barrier(world):
 
 # ------------------------------------------------------------ CPU oracle
 def time_oracle(d, repeats, sample_note):
+    """Time the oracle on the disc as the FP32 path sees it (inputs rounded
+    to float32), so its output is also the parity reference."""
     import oracle
+    import copy
+    d = copy.copy(d)
+    d.sigma_g = d.sigma_g.astype(np.float32).astype(np.float64)
+    if d.sigma_d is not None:
+        d.sigma_d = d.sigma_d.astype(np.float32).astype(np.float64)
     g = oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out)
     plan = oracle.fft64_plan(g, d.h_g, d.h_d if d.sigma_d is not None else None, d.G)
     times, out = [], None
@@ -220,6 +227,9 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     K, W = args.steps, args.warmup
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
+    for e in ev:                     # torch creates the CUDA events on first record
+        for x in e:
+            x.record()
     import ctypes
     for _ in range(W):
         flush.fill_(1.0)
@@ -236,7 +246,8 @@ def run_ours(args):
         flush.fill_(1.0)
         e = ev[k]
         arr = (ctypes.c_void_p * 4)(*[x.cuda_event for x in e[1:5]])
-        lib.sg_set_stage_events(handle, arr)
+        if lib.sg_set_stage_events(handle, arr) != 0:
+            raise RuntimeError("sg_set_stage_events failed")
         e[0].record()
         plan.solve(sg, sd, out=out)
         e[5].record()
@@ -246,8 +257,15 @@ def run_ours(args):
     lib.sg_set_stage_events(handle, None)
     clk = clocks.stop(t_begin, t_end)
     step_ms = [e[0].elapsed_time(e[5]) for e in ev]
-    stage = {"rows_fwd": [e[1].elapsed_time(e[2]) for e in ev], "cols": [e[2].elapsed_time(e[3]) for e in ev],
-             "rows_inv": [e[3].elapsed_time(e[4]) for e in ev]}
+    stage = {"rows_fwd": [], "cols": [], "rows_inv": []}
+    ms3 = (ctypes.c_float * 3)()
+    for e in ev:
+        arr = (ctypes.c_void_p * 4)(*[x.cuda_event for x in e[1:5]])
+        st = lib.sg_stage_times(arr, ms3)
+        if st != 0:
+            raise RuntimeError(f"sg_stage_times failed ({st})")
+        for name, v in zip(stage, ms3):
+            stage[name].append(float(v))
     total_ms = reduce_max(sum(step_ms), world)
     ms_per_step = total_ms / K
     cells_all = d.cells * world

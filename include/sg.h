@@ -161,6 +161,11 @@ int32_t sg_launches_per_solve(const sg_plan *plan, uint32_t outmask);
  * method: events[1..3] after the pair sum).  NULL stops the recording.    */
 sg_status sg_set_stage_events(sg_plan *plan, void *const *events);
 
+/* Durations in milliseconds of the three stages of one solve recorded with
+ * sg_set_stage_events: ms[0] row transforms, ms[1] column pass, ms[2]
+ * inverse row transforms (events[0..3] as recorded; waits for events[3]). */
+sg_status sg_stage_times(void *const *events, float *ms);
+
 /* Release a plan and all its device memory (NULL is a no-op).  Synchronises
  * the device before freeing.                                               */
 void sg_destroy(sg_plan *plan);

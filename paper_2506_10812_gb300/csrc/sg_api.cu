@@ -56,10 +56,15 @@ bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 void free_all(sg_plan *pl)
 {
+    // FP64 plans share one twiddle table between the solve and the table build
+    if (pl->tw_col == pl->tw_col64) pl->tw_col = nullptr;
+    if (pl->tw_row == pl->tw_row64) pl->tw_row = nullptr;
     void *ptrs[] = {pl->tw_col, pl->tw_row, pl->tw_col64, pl->tw_row64, pl->tab, pl->sh, pl->oh,
                     pl->rcen, pl->geo_i, pl->geo_j, pl->Hg, pl->Hd, pl->flag, pl->stage};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    // leave no error state behind for the next call's launch check
+    cudaGetLastError();
 }
 
 template <typename R>
@@ -477,6 +482,20 @@ sg_status sg_set_stage_events(sg_plan *pl, void *const *events)
         if (events && !events[q]) return fail(pl, SG_ERR_ARG, "stage event %d is NULL", q);
         pl->ev[q] = events ? (cudaEvent_t)events[q] : nullptr;
     }
+    return SG_OK;
+}
+
+sg_status sg_stage_times(void *const *events, float *ms)
+{
+    if (!events || !ms) return SG_ERR_ARG;
+    for (int q = 0; q < 4; ++q)
+        if (!events[q]) return SG_ERR_ARG;
+    if (cudaEventSynchronize((cudaEvent_t)events[3]) != cudaSuccess) return SG_ERR_CUDA;
+    for (int q = 0; q < 3; ++q)
+        if (cudaEventElapsedTime(&ms[q], (cudaEvent_t)events[q], (cudaEvent_t)events[q + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            return SG_ERR_CUDA;
+        }
     return SG_OK;
 }
 
