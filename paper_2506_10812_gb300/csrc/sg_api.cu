@@ -27,7 +27,7 @@ struct sg_plan {
     void *tab = nullptr, *sh = nullptr, *oh = nullptr;
     void *rcen = nullptr, *geo_i = nullptr, *geo_j = nullptr;
     void *Hg = nullptr, *Hd = nullptr;
-    unsigned int *flag = nullptr;
+    unsigned int *flag = nullptr;         // bit 1: non-finite output, bit 2: staging timeout
     void *stage = nullptr;                // sg_solve_host: [2 inputs + 6 outputs][cells]
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events
     char err[256] = {0};
@@ -148,6 +148,10 @@ sg_status check_device(sg_plan *pl)
     return SG_OK;
 }
 
+// Radial scaling exponent of the FFT path (see sg_kernels.cu): sources times
+// r, kernel tables times e^{Delta}, accelerations divided by r.
+constexpr double kAlpha = 1.0;
+
 // Build the packed kernel spectra of every ordered fluid pair (App. C
 // lattice kernels, Sec. 5.2 precomputation).
 sg_status build_tables(sg_plan *pl, cudaStream_t s)
@@ -166,7 +170,7 @@ sg_status build_tables(sg_plan *pl, cudaStream_t s)
     // -G du dphi from the cell measure, 1/(L nphi) from the unnormalised
     // forward and inverse transforms
     const double scale = -pl->p.G * pl->du * pl->dphi / ((double)L * nphi);
-    const size_t tab_one = (size_t)(N + 1) * nr * 2 * pl->esz;
+    const size_t tab_one = (size_t)(N + 1) * tab_pitch(nr) * 2 * pl->esz;
     sg_status st = SG_OK;
     for (int a = 0; a < pl->nsrc && st == SG_OK; ++a) {
         for (int b = 0; b < pl->nsrc && st == SG_OK; ++b) {
@@ -174,9 +178,9 @@ sg_status build_tables(sg_plan *pl, cudaStream_t s)
             const double hb = b == 0 ? pl->p.h_g : pl->p.h_d;
             double *o64[3] = {eval, eval + lat, eval + 2 * lat};
             float *o32[3] = {nullptr, nullptr, nullptr};
-            e = launch_tab_eval(nr, nphi, pl->du, ha, hb, scale, !pl->f64, o64, o32, s);
+            e = launch_tab_eval(nr, nphi, pl->du, ha, hb, scale, kAlpha, !pl->f64, o64, o32, s);
             for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
-                e = launch_rows_fwd<double>(o64[c], nullptr, 1, spec, L, nphi, pl->tw_row64, s);
+                e = launch_rows_fwd<double>(o64[c], nullptr, 1, spec, L, nphi, pl->tw_row64, nullptr, false, s);
                 if (e != cudaSuccess) break;
                 char *dst = (char *)pl->tab + (size_t)((a * pl->nsrc + b) * 3 + c) * tab_one;
                 e = pl->f64 ? launch_tabcols<double>(spec, dst, L, nphi, c == 2, pl->tw_col64, s)
@@ -211,10 +215,11 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
     const bool ev = pl->ev[0] != nullptr;
     if (ev) cudaEventRecord(pl->ev[0], s);
     if (pl->p.method == SG_METHOD_FFT) {
-        e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row, s);
+        e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row,
+                               (const R *)pl->rcen, true, s);
         if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
         if (ev) cudaEventRecord(pl->ev[1], s);
-        e = launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->tw_col, s);
+        e = launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->tw_col, pl->flag, s);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
         RowOut ro{};
@@ -343,7 +348,8 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
             SG_TRY(upload(&pl->tw_row, twiddles<float>(p->nphi), s), "twiddles");
         }
         const size_t cbytes = 2 * pl->esz;
-        SG_TRY(cudaMalloc(&pl->tab, (size_t)pl->nsrc * pl->nsrc * 3 * (pl->N + 1) * p->nr * cbytes), "kernel spectra");
+        SG_TRY(cudaMalloc(&pl->tab, (size_t)pl->nsrc * pl->nsrc * 3 * (pl->N + 1) * tab_pitch(p->nr) * cbytes),
+               "kernel spectra");
         SG_TRY(cudaMalloc(&pl->sh, (size_t)pl->nsrc * pl->N * p->nr * cbytes), "scratch");
         SG_TRY(cudaMalloc(&pl->oh, (size_t)pl->nsrc * 3 * pl->N * p->nr * cbytes), "scratch");
         sg_status st = build_tables(pl, s);
@@ -398,7 +404,7 @@ sg_status sg_kernel_table(sg_plan *pl, int pair, int comp, void *out_dev, void *
     float *o32[3] = {nullptr, nullptr, nullptr};
     if (pl->f64) o64[comp] = (double *)out_dev;
     else o32[comp] = (float *)out_dev;
-    cudaError_t e = launch_tab_eval(pl->p.nr, pl->p.nphi, pl->du, ha, hb, 1.0, !pl->f64, o64, o32,
+    cudaError_t e = launch_tab_eval(pl->p.nr, pl->p.nphi, pl->du, ha, hb, 1.0, 0.0, !pl->f64, o64, o32,
                                     (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(pl, e, "kernel table");
     return SG_OK;
@@ -471,7 +477,8 @@ sg_status sg_sync(sg_plan *pl, void *stream)
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->flag, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(pl, e, "sg_sync");
-    if (h) return fail(pl, SG_ERR_NONFINITE, "non-finite value in an output");
+    if (h & 2u) return fail(pl, SG_ERR_TIMEOUT, "a staged kernel-spectrum copy did not complete");
+    if (h & 1u) return fail(pl, SG_ERR_NONFINITE, "non-finite value in an output");
     return SG_OK;
 }
 

@@ -14,33 +14,36 @@ int row_rpc(int nphi, bool f64);
 size_t row_smem_bytes(int nphi, int rpc, bool f64);
 size_t col_smem_bytes(int nr, int nsrc, bool f64);
 size_t tabcol_smem_bytes(int L, bool f64);
+__host__ __device__ int tab_pitch(int nr);   // complex slots per stored kernel-spectrum column (nr + 2)
 cudaError_t set_smem_limits(int max_optin);
 
 // Kernel-table evaluation (App. C lattice), one ordered pair (source aspect
-// ratio ha, target hb), all three components scaled by `scale`, written as
-// [2 nr][nphi] arrays of type double (out64) or float (out32); NULL skips.
-// mixed: evaluate the Bessel functions in FP32 where X >= 1 outside the
-// nearest-neighbour stencil, FP64 elsewhere; otherwise FP64 everywhere.
+// ratio ha, target hb), all three components times scale * e^{alpha Delta},
+// written as [2 nr][nphi] arrays of type double (out64) or float (out32);
+// NULL skips.  mixed: evaluate the Bessel functions in FP32 where X >= 1
+// outside the nearest-neighbour stencil, FP64 elsewhere; otherwise FP64.
 cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, double scale,
-                            bool mixed, double *o64[3], float *o32[3], cudaStream_t s);
+                            double alpha, bool mixed, double *o64[3], float *o32[3], cudaStream_t s);
 
-// Row R2C of `nsrc` real [nrows][nphi] arrays x[a] into the transposed
-// packed spectra xh + a * (nphi/2) * nrows laid out [nphi/2][nrows]
+// Row R2C of `nsrc` real [nrows][nphi] arrays x[a] (each row times
+// rscale[row] when rscale != NULL; row mean removed when dc) into packed
+// spectra xh + a * (nphi/2) * nrows, column-blocked [nphi/2][nrows]
 // (slot m = 0 packs the real m = 0 and m = nphi/2 coefficients).
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
-                            const void *tw_row, cudaStream_t s);
+                            const void *tw_row, const R *rscale, bool dc, cudaStream_t s);
 
 // Column pass of the solve: forward padded FFT of every source column,
 // products with the packed kernel spectra, inverse FFT of every requested
 // (target, component), rows 0..nr-1 kept.
+// flag: bit 2 set when a staged copy never completed (bounded wait).
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
-                        uint32_t outmask, const void *tw_col, cudaStream_t s);
+                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s);
 
-// Column FFT of a table's row spectra ([nphi/2][L] complex double) and
-// packing into [nphi/2 + 1][L/2] complex of type R; `odd` for the sin(psi)
-// component (stored multiplied by i).
+// Column FFT of a table's row spectra (column-blocked [nphi/2][L] complex
+// double) and packing into [nphi/2 + 1][tab_pitch(L/2)] complex of type R;
+// `odd` for the sin(psi) component (stored multiplied by i).
 template <typename R>
 cudaError_t launch_tabcols(const void *spec, void *tab, int L, int nphi, bool odd,
                            const void *tw_col64, cudaStream_t s);
@@ -53,7 +56,8 @@ struct RowOut {
 };
 
 // Inverse row transforms (C2R) of the column-pass output and the epilogue
-// (potential times r_i; finite check into *flag when flag != NULL).
+// (accelerations divided by r_i, undoing the radial source scaling; finite
+// check into *flag bit 1 when flag != NULL).
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
                             const R *rcen, unsigned int *flag, cudaStream_t s);

@@ -1,27 +1,47 @@
 // FFT-convolution path of the thin-disc self-gravity solver (Sec. 5.2 and
 // App. C of Rendon Restrepo et al. 2025) for sm_103a.
 //
-// Data flow of one solve (constant aspect ratios, nr x nphi grid, L = 2 nr):
-//   rows_fwd  each source Sigma_a [nr][nphi] -> row R2C (length nphi) ->
-//             packed spectra written transposed, [nphi/2][nr] complex
-//             (column m = 0 holds the real m = 0 and m = nphi/2 rows as
-//             re + i im);
+// Data flow of one solve (constant aspect ratios, nr x nphi grid, L = 2 nr,
+// N = nphi / 2, H = nr):
+//   rows_fwd  each source Sigma_a [nr][nphi], scaled by r_i (see below) and
+//             with its row mean removed -> row R2C (length nphi) -> packed
+//             spectra (column m = 0 holds the real m = 0 and m = nphi/2
+//             coefficients as re + i im) stored column-blocked;
 //   cols      per column m: zero-padded length-L forward FFT of every
-//             source, products with the packed kernel spectra summed over
+//             source, products with the kernel spectra (staged in shared
+//             memory by TMA bulk copies issued at kernel start) summed over
 //             sources (Sec. 5.2 multi-fluid sums), inverse FFT of every
-//             requested (target, component), rows 0..nr-1 written
-//             [nphi/2][nr];
-//   rows_inv  per output row: packed C2R (length nphi) and the epilogue
-//             (Phi times r_i), written [nr][nphi].
+//             requested (target, component), rows 0..nr-1 written back;
+//   rows_inv  per output row: packed C2R (length nphi) and the epilogue.
+//
+// Column-blocked layout of the [N][rows] intermediates: element (m, i) at
+// ((m / 4) rows + i) 4 + m % 4, so a row transform that owns 4 consecutive
+// rows moves whole 128-byte lines, and a column is a stride-4 vector.
+//
+// Radial scaling: the lattice kernels carry e^{-3 Delta / 2}, which makes
+// the convolution output span (r_out / r_in)^{3/2} across the grid while
+// FP32 FFT rounding is uniform in absolute terms.  With
+// e^{-alpha Delta} = (r' / r)^alpha the convolution is rewritten exactly as
+//     sum_i' Sigma(i') K(i - i') = r_i^-alpha sum_i' [Sigma(i') r_i'^alpha] [e^{alpha Delta} K](i - i'),
+// alpha = 1: the sources are multiplied by r_i' in rows_fwd, the kernel
+// tables by e^Delta, and the accelerations by 1/r_i in rows_inv (the
+// potential's own r_i prefactor cancels the 1/r_i).  Removing each row's
+// mean before the row FFT (and adding nphi * mean back to the m = 0
+// coefficient) is exact by linearity and keeps the small m != 0 modes of a
+// nearly axisymmetric disc from inheriting the rounding of the mean.
+//
 // The kernel spectra (built once per plan by tab_eval -> rows_fwd<double>
 // -> tabcols) already carry -G du dphi / (L nphi), the FFT normalisation.
 #include <math.h>
+#include <stdint.h>
 
 #include "sg_bessel.cuh"
 #include "sg_fft.cuh"
 #include "sg_internal.h"
 
 namespace sg {
+
+constexpr int BW = 4;   // columns per block of the column-blocked layout
 
 // ----------------------------------------------------------------- sizes
 int row_rpc(int nphi, bool f64)
@@ -35,19 +55,29 @@ int row_rpc(int nphi, bool f64)
 
 size_t row_smem_bytes(int nphi, int rpc, bool f64)
 {
-    return (size_t)rpc * padded_len(nphi / 2) * (f64 ? 16 : 8);
+    return (size_t)rpc * padded_len(nphi / 2) * (f64 ? 16 : 8) + 64 * sizeof(double);
 }
+
+__host__ __device__ int tab_pitch(int nr) { return nr + 2; }
+
+__host__ __device__ static inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 size_t col_smem_bytes(int nr, int nsrc, bool f64)
 {
+    const size_t esz = f64 ? 16 : 8;
     const int L = 2 * nr;
-    return ((size_t)padded_len(L) + (size_t)nsrc * L) * (f64 ? 16 : 8);
+    const size_t xb = align16((size_t)padded_len(L) * esz);
+    const size_t tb = (size_t)nsrc * 3 * tab_pitch(nr) * esz;
+    const size_t spec = nsrc == 2 ? (size_t)2 * L * esz : 0;   // gas + dust spectra live in shared memory
+    // column 0 keeps its source spectra in the table area instead
+    const size_t col0 = (size_t)nsrc * L * esz;
+    return 16 + xb + (tb > col0 ? tb : col0) + spec;
 }
 
 size_t tabcol_smem_bytes(int L, bool) { return (size_t)padded_len(L) * 16; }
 
 // Swizzled [N][rpc] transpose tile: conflict-free for both the per-row
-// strided access (consecutive k, fixed row) and the chunked copy.
+// strided access (consecutive k, fixed row) and the blocked copy.
 template <typename C>
 __device__ __forceinline__ int tile_idx(int k, int g, int rpc)
 {
@@ -56,9 +86,15 @@ __device__ __forceinline__ int tile_idx(int k, int g, int rpc)
     return k * rpc + (g ^ ((k >> sh) & (rpc - 1)));
 }
 
+// column-blocked index of element (m, i) in a [N][nrows] intermediate
+__device__ __forceinline__ size_t blk(int m, int i, int nrows)
+{
+    return ((size_t)(m >> 2) * nrows + i) * BW + (m & (BW - 1));
+}
+
 // ----------------------------------------------------------- kernel table
 __global__ void __launch_bounds__(256)
-k_tab_eval(int nr, int nphi, double du, double ha, double hb, double scale, int mixed,
+k_tab_eval(int nr, int nphi, double du, double ha, double hb, double scale, double alpha, int mixed,
            double *p0, double *p1, double *p2, float *q0, float *q1, float *q2)
 {
     __shared__ BesselWeights bw;
@@ -93,7 +129,7 @@ k_tab_eval(int nr, int nphi, double du, double ha, double hb, double scale, int 
                 Dx = b;
             }
             const double hab = sqrt(hab2);
-            const double e32 = scale * exp(-1.5 * Dl);
+            const double e32 = scale * exp((alpha - 1.5) * Dl);
             vP = e32 * k0e * (0.5 * inv_sqrt_pi) / hab;
             const double c = e32 * Dx * (0.125 * inv_sqrt_pi) / (hab2 * hab);
             vR = c * (expm1(Dl) + 2.0 * sp2);
@@ -109,25 +145,28 @@ k_tab_eval(int nr, int nphi, double du, double ha, double hb, double scale, int 
 }
 
 cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, double scale,
-                            bool mixed, double *o64[3], float *o32[3], cudaStream_t s)
+                            double alpha, bool mixed, double *o64[3], float *o32[3], cudaStream_t s)
 {
     const size_t n = (size_t)2 * nr * nphi;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_tab_eval<<<blocks, 256, 0, s>>>(nr, nphi, du, ha, hb, scale, mixed ? 1 : 0, o64[0], o64[1],
+    k_tab_eval<<<blocks, 256, 0, s>>>(nr, nphi, du, ha, hb, scale, alpha, mixed ? 1 : 0, o64[0], o64[1],
                                       o64[2], o32[0], o32[1], o32[2]);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ row R2C
+// rscale: optional per-row multiplier (the radial scaling r_i); dc: remove
+// the row mean before the transform.
 template <typename R>
 __global__ void __launch_bounds__(512)
 k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restrict__ xh, int nrows,
-           int nphi, int rpc, const cplx<R> *__restrict__ tw)
+           int nphi, int rpc, const cplx<R> *__restrict__ tw, const R *__restrict__ rscale, int dc)
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);
+    R *red = reinterpret_cast<R *>(smem_raw);                 // 64 reals: per-warp partial sums
+    C *sm = reinterpret_cast<C *>(smem_raw + 64 * sizeof(double));
     const int N = nphi >> 1, T = N >> 4;
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int a = blockIdx.y;
@@ -135,8 +174,32 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
     const C *xr = reinterpret_cast<const C *>((a == 0 ? x0 : x1) + (size_t)(i0 + g) * nphi);
     C *xb = sm + g * padded_len(N);
     C v[16];
+    const R sc = rscale ? rscale[i0 + g] : (R)1;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = xr[t + T * e];    // z[n] = x[2n] + i x[2n+1]
+    for (int e = 0; e < 16; ++e) {                        // z[n] = x[2n] + i x[2n+1]
+        const C z = xr[t + T * e];
+        v[e] = mkc<C>(z.x * sc, z.y * sc);
+    }
+    R mean = 0;
+    if (dc) {
+        R s = 0;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) s += v[e].x + v[e].y;
+        // reduce over the T threads of this row (aligned power-of-two segment)
+        const int seg = T < 32 ? T : 32;
+        const unsigned lanes = blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u);
+        for (int o = seg >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(lanes, s, o);
+        if (T > 32) {
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+            __syncthreads();
+            s = 0;
+            const int w0 = (g * T) >> 5, nw = T >> 5;
+            for (int w = 0; w < nw; ++w) s += red[w0 + w];
+        }
+        mean = s / (R)nphi;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = mkc<C>(v[e].x - mean, v[e].y - mean);
+    }
     fft_reg<true>(v, N, T, t, xb, tw, 2);
     // X[k] = E[k] + W^k O[k], E = (Z[k] + Z*[N-k]) / 2, O = (Z[k] - Z*[N-k]) / 2i
     __syncthreads();
@@ -148,7 +211,8 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
         const int k = t + T * e;
         const C Z = v[e];
         if (k == 0) {
-            v[e] = mkc<C>(Z.x + Z.y, Z.x - Z.y);          // (X[0], X[nphi/2]) packed
+            // (X[0], X[nphi/2]) packed; the mean only enters X[0]
+            v[e] = mkc<C>(Z.x + Z.y + mean * (R)nphi, Z.x - Z.y);
         } else {
             const C Zc = cconj(xb[pidx(N - k)]);
             const C E = cscale(cadd(Z, Zc), (R)0.5);
@@ -156,125 +220,251 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
             v[e] = cadd(E, cmul(O, __ldg(&tw[k])));
         }
     }
-    // transposed write through a [N][rpc] tile: rpc consecutive rows per m
+    // column-blocked write through a [N][rpc] tile: rpc rows x 4 columns per line
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 16; ++e) sm[tile_idx<C>(t + T * e, g, rpc)] = v[e];
     __syncthreads();
-    C *out = xh + (size_t)a * N * nrows + i0;
+    C *out = xh + (size_t)a * N * nrows;
+    const int per = rpc * BW;
     for (int idx = threadIdx.x; idx < N * rpc; idx += blockDim.x) {
-        const int k = idx / rpc, gg = idx - k * rpc;
-        out[(size_t)k * nrows + gg] = sm[tile_idx<C>(k, gg, rpc)];
+        const int bb = idx / per, rem = idx - bb * per;
+        const int gg = rem / BW, c = rem - gg * BW;
+        out[((size_t)bb * nrows + i0 + gg) * BW + c] = sm[tile_idx<C>(bb * BW + c, gg, rpc)];
     }
 }
 
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
-                            const void *tw_row, cudaStream_t s)
+                            const void *tw_row, const R *rscale, bool dc, cudaStream_t s)
 {
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
     dim3 grid(nrows / rpc, nsrc);
     k_rows_fwd<R><<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
-        x0, x1, (cplx<R> *)xh, nrows, nphi, rpc, (const cplx<R> *)tw_row);
+        x0, x1, (cplx<R> *)xh, nrows, nphi, rpc, (const cplx<R> *)tw_row, rscale, dc ? 1 : 0);
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------- packed table access
-// Packed Hermitian column: slot 0 = (S(0), S(H)), slot k = S(k) for 0<k<H;
-// S(k) for k > H is conj(S(L - k)).  `upper`: k >= H.
-template <typename C>
-__device__ __forceinline__ C tab_at(const C *__restrict__ col, int k, int H, bool upper)
+// ------------------------------------------- TMA bulk copy + mbarrier
+__device__ __forceinline__ unsigned smem_u32(const void *p)
 {
-    const int idx = upper ? (2 * H - k) : k;
-    const int id = idx & (H - 1);
-    const C v = __ldg(&col[id]);
-    if (id == 0) return mkc<C>(upper ? v.y : v.x, 0);
-    return upper ? cconj(v) : v;
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after 2^22 polls (far beyond any copy time),
+// records bit 2 (timeout) in *flag and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned int *flag)
+{
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (flag) atomicOr(flag, 2u);
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---------------------------------------------------------- column pass
+// Kernel spectrum of one (pair, component, column m): P = H + 2 complex,
+// slot k = S(k) for 0 <= k <= H (S(0), S(H) real); S(k > H) = conj(S(L - k)).
+template <typename C>
+__device__ __forceinline__ C spec_at(const C *col, int k, int H, bool upper)
+{
+    return upper ? cconj(col[2 * H - k]) : col[k];
 }
 
-// --------------------------------------------------------- column pass
+// Column m = 0 holds the packed (m = 0, m = nphi/2) pair of real columns:
+// Z = A + i B, so P = A S0 + i B SN = ((Z + Z*(-k)) S0 + (Z - Z*(-k)) SN) / 2.
 template <typename R, int NS>
-__global__ void __launch_bounds__(512)
-k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh,
-       int nr, int N, uint32_t outmask, const cplx<R> *__restrict__ tw)
+__device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
+                                       cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
+                                       const cplx<R> *__restrict__ tw, cplx<R> *xb, cplx<R> *spec)
 {
     using C = cplx<R>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *xb = reinterpret_cast<C *>(smem_raw);
-    const int L = 2 * nr, T = L >> 4, H = nr;
-    const int t = threadIdx.x, m = blockIdx.x;
-    C *spec = xb + padded_len(L);
+    const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
+    const int t = threadIdx.x;
     C v[16];
-#pragma unroll 1
     for (int a = 0; a < NS; ++a) {
-        const C *col = sh + ((size_t)a * N + m) * nr;
+        const C *col = sh + (size_t)a * N * nr;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = col[t + T * e];
+        for (int e = 0; e < 8; ++e) v[e] = col[blk(0, t + T * e, nr)];
 #pragma unroll
-        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
+        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
         fft_reg<true>(v, L, T, t, xb, tw, 1);
 #pragma unroll
         for (int e = 0; e < 16; ++e) spec[a * L + t + T * e] = v[e];
     }
     __syncthreads();
-#pragma unroll 1
     for (int b = 0; b < NS; ++b) {
-#pragma unroll 1
         for (int c = 0; c < 3; ++c) {
             if (!((outmask >> (3 * b + c)) & 1u)) continue;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
                 const int k = t + T * e;
                 C acc = mkc<C>(0, 0);
-#pragma unroll
                 for (int a = 0; a < NS; ++a) {
-                    const C *tc = tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1)) * nr;
+                    const C *t0 = tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1)) * P;
+                    const C *tn = t0 + (size_t)N * P;
                     const C Z = spec[a * L + k];
-                    if (m != 0) {
-                        C S = tab_at(tc + (size_t)m * nr, k, H, e >= 8);
-                        if (c == 2) S = cmul_mi(S);               // K_phi spectrum = -i S
-                        acc = cfma(Z, S, acc);
-                    } else {
-                        // packed column: Z = A + iB with A, B the spectra of the
-                        // real m = 0 and m = nphi/2 columns
-                        const C Zm = cconj(spec[a * L + ((L - k) & (L - 1))]);
-                        C S0 = tab_at(tc, k, H, e >= 8);
-                        C SN = tab_at(tc + (size_t)N * nr, k, H, e >= 8);
-                        if (c == 2) {
-                            S0 = cmul_mi(S0);
-                            SN = cmul_mi(SN);
-                        }
-                        acc = cadd(acc, cscale(cadd(cmul(cadd(Z, Zm), S0), cmul(csub(Z, Zm), SN)), (R)0.5));
+                    const C Zm = cconj(spec[a * L + ((L - k) & (L - 1))]);
+                    C S0 = spec_at(t0, k, H, e >= 8), SN = spec_at(tn, k, H, e >= 8);
+                    if (c == 2) {
+                        S0 = cmul_mi(S0);
+                        SN = cmul_mi(SN);
                     }
+                    acc = cadd(acc, cscale(cadd(cmul(cadd(Z, Zm), S0), cmul(csub(Z, Zm), SN)), (R)0.5));
                 }
                 v[e] = acc;
             }
             fft_reg<false>(v, L, T, t, xb, tw, 1);
-            C *o = oh + ((size_t)(b * 3 + c) * N + m) * nr;
+            C *o = oh + (size_t)(b * 3 + c) * N * nr;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) o[t + T * e] = v[e];       // rows 0..nr-1 only
+            for (int e = 0; e < 8; ++e) o[blk(0, t + T * e, nr)] = v[e];
+        }
+    }
+}
+
+template <typename R, int NS>
+__global__ void __launch_bounds__(512)
+k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr,
+       int N, uint32_t outmask, const cplx<R> *__restrict__ tw, unsigned int *flag)
+{
+    using C = cplx<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
+    C *xb = reinterpret_cast<C *>(smem_raw + 16);
+    C *tb = reinterpret_cast<C *>(smem_raw + 16 + align16((size_t)padded_len(L) * sizeof(C)));
+    const int t = threadIdx.x, m = blockIdx.x;
+    if (m == 0) {
+        // column 0 keeps its source spectra in the table area
+        col0_path<R, NS>(sh, tab, oh, nr, N, outmask, tw, xb, tb);
+        return;
+    }
+    C *sspec = tb + (size_t)NS * 3 * P;           // NS == 2: source spectra in shared memory
+
+    // Stage the kernel spectra of target b (requested components only).
+    auto issue = [&](int b) {
+        if (t == 0) {
+            unsigned bytes = 0;
+            for (int c = 0; c < 3; ++c)
+                if ((outmask >> (3 * b + c)) & 1u) bytes += NS * P * sizeof(C);
+            mbar_expect_tx(bar, bytes);
+            int slot = 0;
+            for (int c = 0; c < 3; ++c) {
+                if (!((outmask >> (3 * b + c)) & 1u)) continue;
+                for (int a = 0; a < NS; ++a, ++slot)
+                    tma_load_1d(tb + (size_t)slot * P,
+                                tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1) + m) * P, P * sizeof(C), bar);
+            }
+        }
+    };
+    if (t == 0) mbar_init(bar, 1);
+    __syncthreads();
+    issue(0);                                      // lands while the forward FFTs run
+
+    C v[16];
+    C spec[NS == 1 ? 16 : 1];                      // NS == 1: source spectrum in registers
+#pragma unroll 1
+    for (int a = 0; a < NS; ++a) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = sh[(size_t)a * N * nr + blk(m, t + T * e, nr)];
+#pragma unroll
+        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
+        fft_reg<true>(v, L, T, t, xb, tw, 1);
+        if constexpr (NS == 1) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) spec[e] = v[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sspec[a * L + t + T * e] = v[e];
+        }
+    }
+#pragma unroll 1
+    for (int b = 0; b < NS; ++b) {
+        if (b > 0) {
+            // every read of the previous stage precedes the TMA rewrite
+            __syncthreads();
+            fence_proxy_async();
+            issue(b);
+        }
+        const bool ok = mbar_wait_bounded(bar, (unsigned)(b & 1), flag);
+        if (__syncthreads_or(!ok)) return;          // the copy never completed: give up on this column
+        int slot = 0;
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            if (!((outmask >> (3 * b + c)) & 1u)) continue;
+            const C *tcol = tb + (size_t)slot * NS * P;
+            slot++;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int k = t + T * e;
+                C acc = mkc<C>(0, 0);
+#pragma unroll
+                for (int a = 0; a < NS; ++a) {
+                    C S = spec_at(tcol + a * P, k, H, e >= 8);
+                    if (c == 2) S = cmul_mi(S);                   // K_phi spectrum = -i S
+                    C Z;
+                    if constexpr (NS == 1) Z = spec[e];
+                    else Z = sspec[a * L + k];
+                    acc = cfma(Z, S, acc);
+                }
+                v[e] = acc;
+            }
+            fft_reg<false>(v, L, T, t, xb, tw, 1);
+            C *o = oh + (size_t)(b * 3 + c) * N * nr;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) o[blk(m, t + T * e, nr)] = v[e];   // rows 0..nr-1 only
         }
     }
 }
 
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
-                        uint32_t outmask, const void *tw_col, cudaStream_t s)
+                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s)
 {
     const bool f64 = sizeof(R) == 8;
     const int N = nphi / 2, T = (2 * nr) / 16;
     const size_t smem = col_smem_bytes(nr, nsrc, f64);
     if (nsrc == 1)
         k_cols<R, 1><<<N, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N,
-                                       outmask, (const cplx<R> *)tw_col);
+                                       outmask, (const cplx<R> *)tw_col, flag);
     else
         k_cols<R, 2><<<N, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N,
-                                       outmask, (const cplx<R> *)tw_col);
+                                       outmask, (const cplx<R> *)tw_col, flag);
     return cudaGetLastError();
 }
 
 // ------------------------------------------- table column FFT + packing
+// spec: column-blocked [nphi/2][L] row spectra of one real table (FP64);
+// tab: [nphi/2 + 1][P] kernel spectrum columns (slot k = S(k), 0 <= k <= H).
 template <typename R>
 __global__ void __launch_bounds__(512)
 k_tabcols(const double2 *__restrict__ spec, cplx<R> *__restrict__ tab, int L, int N, int odd,
@@ -284,43 +474,37 @@ k_tabcols(const double2 *__restrict__ spec, cplx<R> *__restrict__ tab, int L, in
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *xb = reinterpret_cast<double2 *>(smem_raw);
     const int T = L >> 4, H = L >> 1, t = threadIdx.x, m = blockIdx.x;
+    const int P = H + 2;
     double2 v[16];
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] = spec[(size_t)m * L + t + T * e];
+    for (int e = 0; e < 16; ++e) v[e] = spec[blk(m, t + T * e, L)];
     fft_reg<true>(v, L, T, t, xb, tw, 1);
     // the spectrum goes back to the (now free) exchange buffer, padded index
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 16; ++e) xb[pidx(t + T * e)] = v[e];
     __syncthreads();
-    auto sp = [&](int k) { return xb[pidx(k)]; };
-    // stored spectrum S = i T for the odd (sin psi) component, T otherwise
+    auto sp = [&](int k) { return xb[pidx(k & (L - 1))]; };
+    // stored spectrum S = i T for the odd (sin psi) component, T otherwise;
+    // S(0) and S(H) are real by symmetry and stored with a zero imaginary part
     auto S = [&](double2 x) { return odd ? cmul_i(x) : x; };
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const int k = t + T * e;
+    auto put = [&](C *col, int k, double2 x) {
+        if (k == 0 || k == H) x.y = 0.0;
+        col[k] = mkc<C>((R)x.x, (R)x.y);
+    };
+    for (int k = t; k <= H; k += T) {
         if (m != 0) {
-            double2 out = S(sp(k));
-            if (k == 0) out = make_double2(out.x, S(sp(H)).x);
-            tab[(size_t)m * H + k] = mkc<C>((R)out.x, (R)out.y);
+            put(tab + (size_t)m * P, k, S(sp(k)));
         } else {
             // unpack columns 0 and nphi/2 from the packed column
-            auto A = [&](int kk) {
-                const double2 X = sp(kk), Xn = cconj(sp((L - kk) & (L - 1)));
-                return cscale(cadd(X, Xn), 0.5);
-            };
-            auto B = [&](int kk) {
-                const double2 X = sp(kk), Xn = cconj(sp((L - kk) & (L - 1)));
-                return cscale(cmul_mi(csub(X, Xn)), 0.5);
-            };
-            double2 a = S(A(k)), b = S(B(k));
-            if (k == 0) {
-                a = make_double2(a.x, S(A(H)).x);
-                b = make_double2(b.x, S(B(H)).x);
-            }
-            tab[k] = mkc<C>((R)a.x, (R)a.y);
-            tab[(size_t)N * H + k] = mkc<C>((R)b.x, (R)b.y);
+            const double2 X = sp(k), Xn = cconj(sp(L - k));
+            put(tab, k, S(cscale(cadd(X, Xn), 0.5)));
+            put(tab + (size_t)N * P, k, S(cscale(cmul_mi(csub(X, Xn)), 0.5)));
         }
+    }
+    if (t == 0) {
+        tab[(size_t)m * P + H + 1] = mkc<C>(0, 0);
+        if (m == 0) tab[(size_t)N * P + H + 1] = mkc<C>(0, 0);
     }
 }
 
@@ -342,15 +526,31 @@ k_rows_inv(const cplx<R> *__restrict__ oh, RowOut o, int nrows, int nphi, int rp
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);
+    C *sm = reinterpret_cast<C *>(smem_raw + 64 * sizeof(double));
     const int N = nphi >> 1, T = N >> 4;
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int q = blockIdx.y;
     const int i0 = blockIdx.x * rpc;
-    const C *src = oh + (size_t)o.src[q] * N * nrows + i0;
-    for (int idx = threadIdx.x; idx < N * rpc; idx += blockDim.x) {
-        const int k = idx / rpc, gg = idx - k * rpc;
-        sm[tile_idx<C>(k, gg, rpc)] = src[(size_t)k * nrows + gg];
+    const C *src = oh + (size_t)o.src[q] * N * nrows;
+    const int per = rpc * BW;
+    {
+        // every thread copies exactly N rpc / blockDim = 16 elements: issue
+        // all 16 loads before the first shared-memory store
+        C tmp[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int idx = threadIdx.x + j * blockDim.x;
+            const int bb = idx / per, rem = idx - bb * per;
+            const int gg = rem / BW, c = rem - gg * BW;
+            tmp[j] = src[((size_t)bb * nrows + i0 + gg) * BW + c];
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int idx = threadIdx.x + j * blockDim.x;
+            const int bb = idx / per, rem = idx - bb * per;
+            const int gg = rem / BW, c = rem - gg * BW;
+            sm[tile_idx<C>(bb * BW + c, gg, rpc)] = tmp[j];
+        }
     }
     __syncthreads();
     // Z'[k] = (X[k] + X*[N-k]) + i (X[k] - X*[N-k]) W^-k  (= 2 Z[k])
@@ -370,7 +570,9 @@ k_rows_inv(const cplx<R> *__restrict__ oh, RowOut o, int nrows, int nphi, int rp
     // synchronises before its first shared-memory write
     fft_reg<false>(v, N, T, t, sm + g * padded_len(N), tw, 2);
     const int i = i0 + g;
-    const R sc = o.is_phi[q] ? rcen[i] : (R)1;
+    // undo the radial source scaling: accelerations / r_i; the potential's
+    // own r_i prefactor cancels it
+    const R sc = o.is_phi[q] ? (R)1 : (R)1 / rcen[i];
     C *out = reinterpret_cast<C *>(reinterpret_cast<R *>(o.ptr[q]) + (size_t)i * nphi);
     bool bad = false;
 #pragma unroll
@@ -411,13 +613,19 @@ cudaError_t set_smem_limits(int max_optin)
     return cudaSuccess;
 }
 
-template cudaError_t launch_rows_fwd<float>(const float *, const float *, int, void *, int, int, const void *, cudaStream_t);
-template cudaError_t launch_rows_fwd<double>(const double *, const double *, int, void *, int, int, const void *, cudaStream_t);
-template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *, cudaStream_t);
-template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *, cudaStream_t);
+template cudaError_t launch_rows_fwd<float>(const float *, const float *, int, void *, int, int, const void *,
+                                            const float *, bool, cudaStream_t);
+template cudaError_t launch_rows_fwd<double>(const double *, const double *, int, void *, int, int, const void *,
+                                             const double *, bool, cudaStream_t);
+template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
+                                        unsigned int *, cudaStream_t);
+template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
+                                         unsigned int *, cudaStream_t);
 template cudaError_t launch_tabcols<float>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_tabcols<double>(const void *, void *, int, int, bool, const void *, cudaStream_t);
-template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const float *, unsigned int *, cudaStream_t);
-template cudaError_t launch_rows_inv<double>(const void *, const RowOut &, int, int, const void *, const double *, unsigned int *, cudaStream_t);
+template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const float *,
+                                            unsigned int *, cudaStream_t);
+template cudaError_t launch_rows_inv<double>(const void *, const RowOut &, int, int, const void *, const double *,
+                                             unsigned int *, cudaStream_t);
 
 }  // namespace sg
