@@ -22,8 +22,9 @@ struct sg_plan {
     double du = 0, dphi = 0;
     int device = 0;
     size_t esz = 4;                       // bytes per real element
-    void *tw_col = nullptr, *tw_row = nullptr;
-    void *tw_col64 = nullptr, *tw_row64 = nullptr;
+    void *tw_row = nullptr, *tw_row64 = nullptr;     // exp(-2 pi i k / nphi), k < nphi
+    void *twp_row = nullptr, *twp_row64 = nullptr;   // per-pass tables, length nphi / 2
+    void *twp_col = nullptr, *twp_col64 = nullptr;   // per-pass tables, length 2 nr
     void *tab = nullptr, *sh = nullptr, *oh = nullptr;
     void *rcen = nullptr, *geo_i = nullptr, *geo_j = nullptr;
     void *Hg = nullptr, *Hd = nullptr;
@@ -57,10 +58,12 @@ bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 void free_all(sg_plan *pl)
 {
     // FP64 plans share one twiddle table between the solve and the table build
-    if (pl->tw_col == pl->tw_col64) pl->tw_col = nullptr;
     if (pl->tw_row == pl->tw_row64) pl->tw_row = nullptr;
-    void *ptrs[] = {pl->tw_col, pl->tw_row, pl->tw_col64, pl->tw_row64, pl->tab, pl->sh, pl->oh,
-                    pl->rcen, pl->geo_i, pl->geo_j, pl->Hg, pl->Hd, pl->flag, pl->stage};
+    if (pl->twp_row == pl->twp_row64) pl->twp_row = nullptr;
+    if (pl->twp_col == pl->twp_col64) pl->twp_col = nullptr;
+    void *ptrs[] = {pl->tw_row, pl->tw_row64, pl->twp_row, pl->twp_row64, pl->twp_col, pl->twp_col64,
+                    pl->tab, pl->sh, pl->oh, pl->rcen, pl->geo_i, pl->geo_j, pl->Hg, pl->Hd, pl->flag,
+                    pl->stage};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     // leave no error state behind for the next call's launch check
@@ -77,6 +80,30 @@ std::vector<R> twiddles(int M)
         v[2 * (size_t)m] = (R)std::cos(a);
         v[2 * (size_t)m + 1] = (R)(-std::sin(a));
     }
+    return v;
+}
+
+// Per-pass Stockham twiddles of a length-L transform (layout in sg_fft.cuh):
+// for the pass with stride Ns and radix R, W_{Ns R}^{r k} at (r - 1) Ns + k.
+template <typename R>
+std::vector<R> pass_twiddles(int L)
+{
+    std::vector<R> v;
+    auto put = [&](int Ns, int Rad) {
+        for (int r = 1; r < Rad; ++r)
+            for (int k = 0; k < Ns; ++k) {
+                const double a = 2.0 * M_PI * (double)r * (double)k / ((double)Ns * Rad);
+                v.push_back((R)std::cos(a));
+                v.push_back((R)(-std::sin(a)));
+            }
+    };
+    int Ns = 16;
+    while (Ns * 16 <= L) {
+        put(Ns, 16);
+        Ns *= 16;
+    }
+    if (Ns < L) put(Ns, L / Ns);
+    if (v.empty()) v.assign(2, (R)0);
     return v;
 }
 
@@ -180,11 +207,12 @@ sg_status build_tables(sg_plan *pl, cudaStream_t s)
             float *o32[3] = {nullptr, nullptr, nullptr};
             e = launch_tab_eval(nr, nphi, pl->du, ha, hb, scale, kAlpha, !pl->f64, o64, o32, s);
             for (int c = 0; c < 3 && e == cudaSuccess; ++c) {
-                e = launch_rows_fwd<double>(o64[c], nullptr, 1, spec, L, nphi, pl->tw_row64, nullptr, false, s);
+                e = launch_rows_fwd<double>(o64[c], nullptr, 1, spec, L, nphi, pl->tw_row64, pl->twp_row64,
+                                            nullptr, false, s);
                 if (e != cudaSuccess) break;
                 char *dst = (char *)pl->tab + (size_t)((a * pl->nsrc + b) * 3 + c) * tab_one;
-                e = pl->f64 ? launch_tabcols<double>(spec, dst, L, nphi, c == 2, pl->tw_col64, s)
-                            : launch_tabcols<float>(spec, dst, L, nphi, c == 2, pl->tw_col64, s);
+                e = pl->f64 ? launch_tabcols<double>(spec, dst, L, nphi, c == 2, pl->twp_col64, s)
+                            : launch_tabcols<float>(spec, dst, L, nphi, c == 2, pl->twp_col64, s);
             }
             if (e != cudaSuccess) st = cuda_fail(pl, e, "kernel table build");
         }
@@ -216,10 +244,10 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
     if (ev) cudaEventRecord(pl->ev[0], s);
     if (pl->p.method == SG_METHOD_FFT) {
         e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row,
-                               (const R *)pl->rcen, true, s);
+                               pl->twp_row, (const R *)pl->rcen, true, s);
         if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
         if (ev) cudaEventRecord(pl->ev[1], s);
-        e = launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->tw_col, pl->flag, s);
+        e = launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
         RowOut ro{};
@@ -230,7 +258,7 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
             ro.is_phi[ro.n] = (q % 3) == SG_COMP_PHI;
             ++ro.n;
         }
-        e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, (const R *)pl->rcen, flag, s);
+        e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s);
         if (e != cudaSuccess) return cuda_fail(pl, e, "inverse row transform");
         if (ev) cudaEventRecord(pl->ev[3], s);
     } else {
@@ -338,14 +366,17 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
     SG_TRY(cudaMalloc((void **)&pl->flag, sizeof(unsigned int)), "flag");
     SG_TRY(cudaMemsetAsync(pl->flag, 0, sizeof(unsigned int), s), "flag");
     if (fft) {
-        SG_TRY(upload(&pl->tw_col64, twiddles<double>(pl->L), s), "twiddles");
         SG_TRY(upload(&pl->tw_row64, twiddles<double>(p->nphi), s), "twiddles");
+        SG_TRY(upload(&pl->twp_row64, pass_twiddles<double>(p->nphi / 2), s), "twiddles");
+        SG_TRY(upload(&pl->twp_col64, pass_twiddles<double>(pl->L), s), "twiddles");
         if (pl->f64) {
-            pl->tw_col = pl->tw_col64;
             pl->tw_row = pl->tw_row64;
+            pl->twp_row = pl->twp_row64;
+            pl->twp_col = pl->twp_col64;
         } else {
-            SG_TRY(upload(&pl->tw_col, twiddles<float>(pl->L), s), "twiddles");
             SG_TRY(upload(&pl->tw_row, twiddles<float>(p->nphi), s), "twiddles");
+            SG_TRY(upload(&pl->twp_row, pass_twiddles<float>(p->nphi / 2), s), "twiddles");
+            SG_TRY(upload(&pl->twp_col, pass_twiddles<float>(pl->L), s), "twiddles");
         }
         const size_t cbytes = 2 * pl->esz;
         SG_TRY(cudaMalloc(&pl->tab, (size_t)pl->nsrc * pl->nsrc * 3 * (pl->N + 1) * tab_pitch(p->nr) * cbytes),

@@ -10,8 +10,11 @@
 // same strided layout, so a forward transform, a pointwise product and an
 // inverse transform need no reordering at all.
 //
-// Twiddles come from a table tw[m] = exp(-2 pi i m / M) (computed in FP64 on
-// the host); a length-L transform uses tw[m * (M / L)].
+// Twiddles come from a per-pass table (computed in FP64 on the host): the
+// pass with stride Ns and radix R reads W_{Ns R}^{r k} = exp(-2 pi i r k / (Ns R))
+// at (r - 1) Ns + k, so the threads of a warp (consecutive k) read
+// consecutive entries; the passes' segments follow one another (Ns = 16,
+// 256, ... for the radix-16 passes, then the final pass).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -83,11 +86,63 @@ template <bool FWD, int P, typename T> __device__ __forceinline__ T w16(T a)
     }
 }
 
+// ---- packed FP32 pairs (Blackwell add/sub/fma.f32x2): one instruction per
+// complex add or subtract.  Results are bit-identical to the scalar forms
+// (each lane is one correctly rounded operation; x * (+-1) is exact).
+__device__ __forceinline__ float2 padd(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+// c + a * (sx, sy) with sx, sy = +-1
+template <int SX, int SY>
+__device__ __forceinline__ float2 pfma_sign(float2 a, float2 c)
+{
+    float2 d;
+    asm("{\n .reg .b64 ra, rs, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rs, {%6, %7};\n"
+        " mov.b64 rc, {%4, %5};\n fma.rn.f32x2 rd, ra, rs, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(c.x), "f"(c.y), "f"((float)SX), "f"((float)SY));
+    return d;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return padd(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return psub(a, b); }
+
 template <bool FWD, typename T> __device__ __forceinline__ void dft2(T &a0, T &a1)
 {
     T t = a0;
     a0 = cadd(t, a1);
     a1 = csub(t, a1);
+}
+
+// Packed radix 4: u = swap(a1 - a3) in scalar form, the +-i rotations as
+// sign-vector FMAs (9 instructions instead of 16).
+template <bool FWD> __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+{
+    const float2 t0 = padd(a0, a2), t1 = psub(a0, a2), t2 = padd(a1, a3);
+    const float2 u = make_float2(a1.y - a3.y, a1.x - a3.x);
+    a0 = padd(t0, t2);
+    a2 = psub(t0, t2);
+    if (FWD) {   // t1 - i t3 = t1 + (u.x, -u.y),  t1 + i t3 = t1 + (-u.x, u.y)
+        a1 = pfma_sign<1, -1>(u, t1);
+        a3 = pfma_sign<-1, 1>(u, t1);
+    } else {
+        a1 = pfma_sign<-1, 1>(u, t1);
+        a3 = pfma_sign<1, -1>(u, t1);
+    }
 }
 
 template <bool FWD, typename T> __device__ __forceinline__ void dft4(T &a0, T &a1, T &a2, T &a3)
@@ -179,16 +234,14 @@ __device__ __forceinline__ void exchange16(T (&v)[16], int t, int T_, int Ns, T 
 // Final Stockham pass of radix RL in {2, 4, 8} (Q = 16 / RL butterflies per
 // thread; butterfly q combines registers q + r Q).  Lands in-register.
 template <bool FWD, int RL, typename T>
-__device__ __forceinline__ void final_pass(T (&v)[16], int t, int T_, int Ns,
-                                           const T *__restrict__ tw, int twstride)
+__device__ __forceinline__ void final_pass(T (&v)[16], int t, int T_, int Ns, const T *__restrict__ tp)
 {
     constexpr int Q = 16 / RL;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int k = (t + T_ * q) & (Ns - 1);
 #pragma unroll
-        for (int r = 1; r < RL; ++r)
-            v[q + r * Q] = twmul<FWD>(v[q + r * Q], __ldg(&tw[(r * k) * twstride]));
+        for (int r = 1; r < RL; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], __ldg(&tp[(r - 1) * Ns + k]));
     }
     if constexpr (RL == 2) {
 #pragma unroll
@@ -207,29 +260,121 @@ __device__ __forceinline__ void final_pass(T (&v)[16], int t, int T_, int Ns,
 // sum x[n] exp(-2 pi i n k / L); inverse: the same with +i (unnormalised).
 // xb: this transform's shared buffer of padded_len(L) elements.  Every thread
 // of the CTA must call this together (it contains __syncthreads).
-// tw: twiddle table exp(-2 pi i m / M) with M = L * twstride.
+// twp: the per-pass twiddle table of length L (see pass_twiddle_count).
 template <bool FWD, typename T>
-__device__ __forceinline__ void fft_reg(T (&v)[16], int L, int T_, int t, T *xb,
-                                        const T *__restrict__ tw, int twstride)
+__device__ __forceinline__ void fft_reg(T (&v)[16], int L, int T_, int t, T *xb, const T *__restrict__ twp)
 {
     dft16<FWD>(v);                              // pass Ns = 1: no twiddles
     if (L == 16) return;
     int Ns = 16;
+    const T *tp = twp;
     exchange16(v, t, T_, 1, xb);
     while (Ns * 16 <= L) {
         const int k = t & (Ns - 1);
-        const int step = (L / (Ns * 16)) * k * twstride;
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = twmul<FWD>(v[r], __ldg(&tw[r * step]));
+        for (int r = 1; r < 16; ++r) v[r] = twmul<FWD>(v[r], __ldg(&tp[(r - 1) * Ns + k]));
         dft16<FWD>(v);
+        tp += 15 * Ns;
         if (Ns * 16 == L) return;
         exchange16(v, t, T_, Ns, xb);
         Ns *= 16;
     }
     const int RL = L / Ns;
-    if (RL == 8) final_pass<FWD, 8>(v, t, T_, Ns, tw, twstride);
-    else if (RL == 4) final_pass<FWD, 4>(v, t, T_, Ns, tw, twstride);
-    else final_pass<FWD, 2>(v, t, T_, Ns, tw, twstride);
+    if (RL == 8) final_pass<FWD, 8>(v, t, T_, Ns, tp);
+    else if (RL == 4) final_pass<FWD, 4>(v, t, T_, Ns, tp);
+    else final_pass<FWD, 2>(v, t, T_, Ns, tp);
+}
+
+// ---------------------------------------------------------------------
+// Compile-time-length variant (L >= 256): same passes and layout as
+// fft_reg, but every stride is a constant, so the shared-memory and twiddle
+// addresses are a per-thread base plus immediate offsets, and outputs the
+// caller never reads are removed by the compiler.
+//   pidx(16 t + r)           = 17 t + r                            (Ns = 1)
+//   pidx(base + r Ns)        = base + (base >> 4) + r (Ns + Ns/16)   (Ns % 16 == 0)
+//   pidx(t + T e)            = t + (t >> 4) + e (T + T/16)         (T % 16 == 0)
+template <int Ns, int TT, typename T>
+__device__ __forceinline__ void exchange_ct(T (&v)[16], int t, T *xb)
+{
+    T *w;
+    constexpr int step = Ns == 1 ? 1 : Ns + Ns / 16;
+    if constexpr (Ns == 1) {
+        w = xb + 17 * t;
+    } else {
+        const int k = t & (Ns - 1);
+        const int base = (t - k) * 16 + k;
+        w = xb + base + (base >> 4);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) w[r * step] = v[r];
+    __syncthreads();
+    const T *rd = xb + t + (t >> 4);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = rd[e * (TT + TT / 16)];
+}
+
+template <bool FWD, int L, int Ns, typename T>
+__device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *__restrict__ tp)
+{
+    constexpr int TT = L / 16;
+    if constexpr (Ns * 16 <= L) {
+        const T *p = tp + (t & (Ns - 1));
+#pragma unroll
+        for (int r = 1; r < 16; ++r) v[r] = twmul<FWD>(v[r], __ldg(p + (r - 1) * Ns));
+        dft16<FWD>(v);
+        if constexpr (Ns * 16 < L) {
+            exchange_ct<Ns, TT>(v, t, xb);
+            fft_ct_pass<FWD, L, Ns * 16>(v, t, xb, tp + 15 * Ns);
+        }
+    } else {
+        constexpr int RL = L / Ns, Q = 16 / RL;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const T *p = tp + ((t + TT * q) & (Ns - 1));
+#pragma unroll
+            for (int r = 1; r < RL; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], __ldg(p + (r - 1) * Ns));
+        }
+        if constexpr (RL == 2) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) dft2<FWD>(v[q], v[q + Q]);
+        } else if constexpr (RL == 4) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) dft4<FWD>(v[q], v[q + Q], v[q + 2 * Q], v[q + 3 * Q]);
+        } else {
+            dft8<FWD, 0, 2>(v);
+            dft8<FWD, 1, 2>(v);
+        }
+    }
+}
+
+template <bool FWD, int L, typename T>
+__device__ __forceinline__ void fft_ct(T (&v)[16], int t, T *xb, const T *__restrict__ twp)
+{
+    static_assert(L >= 256 && (L & (L - 1)) == 0, "compile-time FFT needs a power of two >= 256");
+    dft16<FWD>(v);
+    exchange_ct<1, L / 16>(v, t, xb);
+    fft_ct_pass<FWD, L, 16>(v, t, xb, twp);
+}
+
+// Compile-time length when LC > 0, runtime length L otherwise.
+template <bool FWD, int LC, typename T>
+__device__ __forceinline__ void fft_any(T (&v)[16], int L, int T_, int t, T *xb, const T *__restrict__ twp)
+{
+    if constexpr (LC > 0) fft_ct<FWD, LC>(v, t, xb, twp);
+    else fft_reg<FWD>(v, L, T_, t, xb, twp);
+}
+
+// Number of complex entries of the per-pass twiddle table of length L.
+__host__ __device__ constexpr int pass_twiddle_count(int L)
+{
+    int n = 0, Ns = 16;
+    while (Ns * 16 <= L) {
+        n += 15 * Ns;
+        Ns *= 16;
+    }
+    if (Ns < L) n += (L / Ns - 1) * Ns;
+    return n > 0 ? n : 1;
 }
 
 }  // namespace sg

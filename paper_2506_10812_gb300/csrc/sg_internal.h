@@ -7,6 +7,12 @@
 
 namespace sg {
 
+// Twiddle tables: tw_row[k] = exp(-2 pi i k / nphi), k < nphi (the R2C /
+// C2R pre- and post-processing); twp_row / twp_col / twp_col64: per-pass
+// tables (sg_fft.cuh) of the length-nphi/2 row and length-2nr column
+// transforms.  Every launch below that transforms takes the per-pass table
+// of its own length.
+//
 // Row transforms process RPC rows per CTA (one group of nphi/32 threads per
 // row) so that the transposed [m][row] intermediates move in RPC-element
 // chunks; both the forward and the inverse use the same shared-memory size.
@@ -31,7 +37,7 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 // (slot m = 0 packs the real m = 0 and m = nphi/2 coefficients).
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
-                            const void *tw_row, const R *rscale, bool dc, cudaStream_t s);
+                            const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s);
 
 // Column pass of the solve: forward padded FFT of every source column,
 // products with the packed kernel spectra, inverse FFT of every requested
@@ -60,7 +66,7 @@ struct RowOut {
 // check into *flag bit 1 when flag != NULL).
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
-                            const R *rcen, unsigned int *flag, cudaStream_t s);
+                            const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s);
 
 // Direct pair sum (general scale heights) for one target fluid.
 template <typename R>

@@ -81,15 +81,55 @@ size_t tabcol_smem_bytes(int L, bool) { return (size_t)padded_len(L) * 16; }
 template <typename C>
 __device__ __forceinline__ int tile_idx(int k, int g, int rpc)
 {
-    constexpr int per_wavefront = 128 / sizeof(C);       // 16 (float2) or 8 (double2)
-    const int sh = __ffs(per_wavefront / rpc) - 1;        // log2(per_wavefront / rpc)
-    return k * rpc + (g ^ ((k >> sh) & (rpc - 1)));
+    constexpr int lg_wf = sizeof(C) == 8 ? 4 : 3;         // log2(128 / sizeof(C))
+    const int lg_rpc = rpc == 4 ? 2 : (rpc == 2 ? 1 : 0);
+    return k * rpc + (g ^ ((k >> (lg_wf - lg_rpc)) & (rpc - 1)));
 }
 
 // column-blocked index of element (m, i) in a [N][nrows] intermediate
 __device__ __forceinline__ size_t blk(int m, int i, int nrows)
 {
     return ((size_t)(m >> 2) * nrows + i) * BW + (m & (BW - 1));
+}
+
+// ------------------------------------------------ L2 eviction policies
+// Per-instruction L2 cache hints (createpolicy): the kernel spectra stream
+// through L2 once per solve (evict-first); the column pass's output is read
+// again by the inverse row transforms right after (evict-last), so it should
+// stay in L2 instead of the streamed spectra.
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_hint(float2 *p, float2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_hint(double2 *p, double2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float2 ld_hint(const float2 *p, uint64_t pol)
+{
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_hint(const double2 *p, uint64_t pol)
+{
+    double2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+    return v;
 }
 
 // ----------------------------------------------------------- kernel table
@@ -158,16 +198,20 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 // ------------------------------------------------------------ row R2C
 // rscale: optional per-row multiplier (the radial scaling r_i); dc: remove
 // the row mean before the transform.
-template <typename R>
-__global__ void __launch_bounds__(512)
+// NC > 0: compile-time row transform length (nphi / 2).
+template <typename R, int NC>
+__global__ void __launch_bounds__(512, 2)
 k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restrict__ xh, int nrows,
-           int nphi, int rpc, const cplx<R> *__restrict__ tw, const R *__restrict__ rscale, int dc)
+           int nphi_rt, int rpc, const cplx<R> *__restrict__ tw, const cplx<R> *__restrict__ twp,
+           const R *__restrict__ rscale, int dc)
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *red = reinterpret_cast<R *>(smem_raw);                 // 64 reals: per-warp partial sums
     C *sm = reinterpret_cast<C *>(smem_raw + 64 * sizeof(double));
+    const int nphi = NC > 0 ? 2 * NC : nphi_rt;
     const int N = nphi >> 1, T = N >> 4;
+    if (NC > 0) rpc = 4;                                        // row_rpc(2 NC) for NC <= 2048
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int a = blockIdx.y;
     const int i0 = blockIdx.x * rpc;
@@ -200,7 +244,7 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
 #pragma unroll
         for (int e = 0; e < 16; ++e) v[e] = mkc<C>(v[e].x - mean, v[e].y - mean);
     }
-    fft_reg<true>(v, N, T, t, xb, tw, 2);
+    fft_any<true, NC>(v, N, T, t, xb, twp);
     // X[k] = E[k] + W^k O[k], E = (Z[k] + Z*[N-k]) / 2, O = (Z[k] - Z*[N-k]) / 2i
     __syncthreads();
 #pragma unroll
@@ -227,22 +271,29 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
     __syncthreads();
     C *out = xh + (size_t)a * N * nrows;
     const int per = rpc * BW;
+    const uint64_t pl = l2_evict_last();
     for (int idx = threadIdx.x; idx < N * rpc; idx += blockDim.x) {
         const int bb = idx / per, rem = idx - bb * per;
         const int gg = rem / BW, c = rem - gg * BW;
-        out[((size_t)bb * nrows + i0 + gg) * BW + c] = sm[tile_idx<C>(bb * BW + c, gg, rpc)];
+        st_hint(out + ((size_t)bb * nrows + i0 + gg) * BW + c, sm[tile_idx<C>(bb * BW + c, gg, rpc)], pl);
     }
 }
 
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
-                            const void *tw_row, const R *rscale, bool dc, cudaStream_t s)
+                            const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s)
 {
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
     dim3 grid(nrows / rpc, nsrc);
-    k_rows_fwd<R><<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
-        x0, x1, (cplx<R> *)xh, nrows, nphi, rpc, (const cplx<R> *)tw_row, rscale, dc ? 1 : 0);
+    auto go = [&](auto kern) {
+        kern<<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
+            x0, x1, (cplx<R> *)xh, nrows, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rscale,
+            dc ? 1 : 0);
+    };
+    if (!f64 && nphi == 4096) go(k_rows_fwd<R, 2048>);
+    else if (!f64 && nphi == 2048) go(k_rows_fwd<R, 1024>);
+    else go(k_rows_fwd<R, 0>);
     return cudaGetLastError();
 }
 
@@ -262,12 +313,13 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
                  : "memory");
 }
 // 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16)
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+// with an L2 cache policy
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, uint64_t *bar, uint64_t pol)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
@@ -317,7 +369,7 @@ __device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cpl
         for (int e = 0; e < 8; ++e) v[e] = col[blk(0, t + T * e, nr)];
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
-        fft_reg<true>(v, L, T, t, xb, tw, 1);
+        fft_reg<true>(v, L, T, t, xb, tw);
 #pragma unroll
         for (int e = 0; e < 16; ++e) spec[a * L + t + T * e] = v[e];
     }
@@ -343,7 +395,7 @@ __device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cpl
                 }
                 v[e] = acc;
             }
-            fft_reg<false>(v, L, T, t, xb, tw, 1);
+            fft_reg<false>(v, L, T, t, xb, tw);
             C *o = oh + (size_t)(b * 3 + c) * N * nr;
 #pragma unroll
             for (int e = 0; e < 8; ++e) o[blk(0, t + T * e, nr)] = v[e];
@@ -351,14 +403,16 @@ __device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cpl
     }
 }
 
-template <typename R, int NS>
+// LC > 0: compile-time column length (2 nr).
+template <typename R, int NS, int LC>
 __global__ void __launch_bounds__(512)
-k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr,
+k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr_rt,
        int N, uint32_t outmask, const cplx<R> *__restrict__ tw, unsigned int *flag)
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    const int nr = LC > 0 ? LC / 2 : nr_rt;
     const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
     C *xb = reinterpret_cast<C *>(smem_raw + 16);
     C *tb = reinterpret_cast<C *>(smem_raw + 16 + align16((size_t)padded_len(L) * sizeof(C)));
@@ -373,6 +427,7 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
     // Stage the kernel spectra of target b (requested components only).
     auto issue = [&](int b) {
         if (t == 0) {
+            const uint64_t pol = l2_evict_first();
             unsigned bytes = 0;
             for (int c = 0; c < 3; ++c)
                 if ((outmask >> (3 * b + c)) & 1u) bytes += NS * P * sizeof(C);
@@ -382,7 +437,7 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
                 if (!((outmask >> (3 * b + c)) & 1u)) continue;
                 for (int a = 0; a < NS; ++a, ++slot)
                     tma_load_1d(tb + (size_t)slot * P,
-                                tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1) + m) * P, P * sizeof(C), bar);
+                                tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1) + m) * P, P * sizeof(C), bar, pol);
             }
         }
     };
@@ -394,11 +449,12 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
     C spec[NS == 1 ? 16 : 1];                      // NS == 1: source spectrum in registers
 #pragma unroll 1
     for (int a = 0; a < NS; ++a) {
+        const uint64_t pf = l2_evict_first();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = sh[(size_t)a * N * nr + blk(m, t + T * e, nr)];
+        for (int e = 0; e < 8; ++e) v[e] = ld_hint(sh + (size_t)a * N * nr + blk(m, t + T * e, nr), pf);
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
-        fft_reg<true>(v, L, T, t, xb, tw, 1);
+        fft_any<true, LC>(v, L, T, t, xb, tw);
         if constexpr (NS == 1) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) spec[e] = v[e];
@@ -438,10 +494,11 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
                 }
                 v[e] = acc;
             }
-            fft_reg<false>(v, L, T, t, xb, tw, 1);
+            fft_any<false, LC>(v, L, T, t, xb, tw);
             C *o = oh + (size_t)(b * 3 + c) * N * nr;
+            const uint64_t pl = l2_evict_last();
 #pragma unroll
-            for (int e = 0; e < 8; ++e) o[blk(m, t + T * e, nr)] = v[e];   // rows 0..nr-1 only
+            for (int e = 0; e < 8; ++e) st_hint(o + blk(m, t + T * e, nr), v[e], pl);   // rows 0..nr-1 only
         }
     }
 }
@@ -453,12 +510,20 @@ cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int n
     const bool f64 = sizeof(R) == 8;
     const int N = nphi / 2, T = (2 * nr) / 16;
     const size_t smem = col_smem_bytes(nr, nsrc, f64);
-    if (nsrc == 1)
-        k_cols<R, 1><<<N, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N,
-                                       outmask, (const cplx<R> *)tw_col, flag);
-    else
-        k_cols<R, 2><<<N, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N,
-                                       outmask, (const cplx<R> *)tw_col, flag);
+    auto go = [&](auto kern) {
+        kern<<<N, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N, outmask,
+                                (const cplx<R> *)tw_col, flag);
+    };
+    const int L = 2 * nr;
+    if (nsrc == 1) {
+        if (!f64 && L == 4096) go(k_cols<R, 1, 4096>);
+        else if (!f64 && L == 2048) go(k_cols<R, 1, 2048>);
+        else go(k_cols<R, 1, 0>);
+    } else {
+        if (!f64 && L == 4096) go(k_cols<R, 2, 4096>);
+        else if (!f64 && L == 2048) go(k_cols<R, 2, 2048>);
+        else go(k_cols<R, 2, 0>);
+    }
     return cudaGetLastError();
 }
 
@@ -478,7 +543,7 @@ k_tabcols(const double2 *__restrict__ spec, cplx<R> *__restrict__ tab, int L, in
     double2 v[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = spec[blk(m, t + T * e, L)];
-    fft_reg<true>(v, L, T, t, xb, tw, 1);
+    fft_reg<true>(v, L, T, t, xb, tw);
     // the spectrum goes back to the (now free) exchange buffer, padded index
     __syncthreads();
 #pragma unroll
@@ -519,15 +584,18 @@ cudaError_t launch_tabcols(const void *spec, void *tab, int L, int nphi, bool od
 }
 
 // ------------------------------------------------------- row C2R + epilogue
-template <typename R>
-__global__ void __launch_bounds__(512)
-k_rows_inv(const cplx<R> *__restrict__ oh, RowOut o, int nrows, int nphi, int rpc,
-           const cplx<R> *__restrict__ tw, const R *__restrict__ rcen, unsigned int *flag)
+template <typename R, int NC>
+__global__ void __launch_bounds__(512, 2)
+k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int nrows, int nphi_rt, int rpc,
+           const cplx<R> *__restrict__ tw, const cplx<R> *__restrict__ twp, const R *__restrict__ rcen,
+           unsigned int *flag)
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw + 64 * sizeof(double));
+    const int nphi = NC > 0 ? 2 * NC : nphi_rt;
     const int N = nphi >> 1, T = N >> 4;
+    if (NC > 0) rpc = 4;                                        // row_rpc(2 NC) for NC <= 2048
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int q = blockIdx.y;
     const int i0 = blockIdx.x * rpc;
@@ -536,13 +604,14 @@ k_rows_inv(const cplx<R> *__restrict__ oh, RowOut o, int nrows, int nphi, int rp
     {
         // every thread copies exactly N rpc / blockDim = 16 elements: issue
         // all 16 loads before the first shared-memory store
+        const uint64_t pf = l2_evict_first();
         C tmp[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int idx = threadIdx.x + j * blockDim.x;
             const int bb = idx / per, rem = idx - bb * per;
             const int gg = rem / BW, c = rem - gg * BW;
-            tmp[j] = src[((size_t)bb * nrows + i0 + gg) * BW + c];
+            tmp[j] = ld_hint(src + ((size_t)bb * nrows + i0 + gg) * BW + c, pf);
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -568,7 +637,7 @@ k_rows_inv(const cplx<R> *__restrict__ oh, RowOut o, int nrows, int nphi, int rp
     }
     // the transform's exchange buffer overlays the tile; fft_reg
     // synchronises before its first shared-memory write
-    fft_reg<false>(v, N, T, t, sm + g * padded_len(N), tw, 2);
+    fft_any<false, NC>(v, N, T, t, sm + g * padded_len(N), twp);
     const int i = i0 + g;
     // undo the radial source scaling: accelerations / r_i; the potential's
     // own r_i prefactor cancels it
@@ -586,13 +655,18 @@ k_rows_inv(const cplx<R> *__restrict__ oh, RowOut o, int nrows, int nphi, int rp
 
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
-                            const R *rcen, unsigned int *flag, cudaStream_t s)
+                            const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s)
 {
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
     dim3 grid(nr / rpc, o.n);
-    k_rows_inv<R><<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
-        (const cplx<R> *)oh, o, nr, nphi, rpc, (const cplx<R> *)tw_row, rcen, flag);
+    auto go = [&](auto kern) {
+        kern<<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
+            (const cplx<R> *)oh, o, nr, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rcen, flag);
+    };
+    if (!f64 && nphi == 4096) go(k_rows_inv<R, 2048>);
+    else if (!f64 && nphi == 2048) go(k_rows_inv<R, 1024>);
+    else go(k_rows_inv<R, 0>);
     return cudaGetLastError();
 }
 
@@ -601,11 +675,15 @@ cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, c
 // can share the kernels.
 cudaError_t set_smem_limits(int max_optin)
 {
-    const void *fns[] = {(const void *)k_rows_fwd<float>,  (const void *)k_rows_fwd<double>,
-                         (const void *)k_rows_inv<float>,  (const void *)k_rows_inv<double>,
-                         (const void *)k_cols<float, 1>,   (const void *)k_cols<float, 2>,
-                         (const void *)k_cols<double, 1>,  (const void *)k_cols<double, 2>,
-                         (const void *)k_tabcols<float>,   (const void *)k_tabcols<double>};
+    const void *fns[] = {(const void *)k_rows_fwd<float, 0>,      (const void *)k_rows_fwd<float, 2048>,
+                         (const void *)k_rows_fwd<float, 1024>,   (const void *)k_rows_fwd<double, 0>,
+                         (const void *)k_rows_inv<float, 0>,      (const void *)k_rows_inv<float, 2048>,
+                         (const void *)k_rows_inv<float, 1024>,   (const void *)k_rows_inv<double, 0>,
+                         (const void *)k_cols<float, 1, 0>,       (const void *)k_cols<float, 1, 4096>,
+                         (const void *)k_cols<float, 1, 2048>,    (const void *)k_cols<float, 2, 0>,
+                         (const void *)k_cols<float, 2, 4096>,    (const void *)k_cols<float, 2, 2048>,
+                         (const void *)k_cols<double, 1, 0>,      (const void *)k_cols<double, 2, 0>,
+                         (const void *)k_tabcols<float>,          (const void *)k_tabcols<double>};
     for (const void *fn : fns) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
         if (e != cudaSuccess) return e;
@@ -614,18 +692,18 @@ cudaError_t set_smem_limits(int max_optin)
 }
 
 template cudaError_t launch_rows_fwd<float>(const float *, const float *, int, void *, int, int, const void *,
-                                            const float *, bool, cudaStream_t);
+                                            const void *, const float *, bool, cudaStream_t);
 template cudaError_t launch_rows_fwd<double>(const double *, const double *, int, void *, int, int, const void *,
-                                             const double *, bool, cudaStream_t);
+                                             const void *, const double *, bool, cudaStream_t);
 template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
                                         unsigned int *, cudaStream_t);
 template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
                                          unsigned int *, cudaStream_t);
 template cudaError_t launch_tabcols<float>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_tabcols<double>(const void *, void *, int, int, bool, const void *, cudaStream_t);
-template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const float *,
-                                            unsigned int *, cudaStream_t);
-template cudaError_t launch_rows_inv<double>(const void *, const RowOut &, int, int, const void *, const double *,
-                                             unsigned int *, cudaStream_t);
+template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const void *,
+                                            const float *, unsigned int *, cudaStream_t);
+template cudaError_t launch_rows_inv<double>(const void *, const RowOut &, int, int, const void *, const void *,
+                                             const double *, unsigned int *, cudaStream_t);
 
 }  // namespace sg

@@ -173,10 +173,11 @@ def test_lognormal_full_size(nr, nphi):
         assert np.abs(ref[k].ravel()[idx] - samp[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
 
 
-def test_lognormal_bifluid_large():
-    d = rounded(inputs.lognormal_bifluid(512, 1024, St=1.0), torch.float32)
+@pytest.mark.parametrize("nr,nphi,St", [(512, 1024, 1.0), (1024, 2048, 0.1)])
+def test_lognormal_bifluid_large(nr, nphi, St):
+    d = rounded(inputs.lognormal_bifluid(nr, nphi, St=St), torch.float32)
     ref = oracle.fft64(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G)
-    assert_close(gpu_solve(d), ref, TOL32, "bif512")
+    assert_close(gpu_solve(d), ref, TOL32, f"bif{nr}")
 
 
 # ------------------------------------------------------------ properties
