@@ -166,6 +166,33 @@ sg_status sg_set_stage_events(sg_plan *plan, void *const *events);
  * inverse row transforms (events[0..3] as recorded; waits for events[3]). */
 sg_status sg_stage_times(void *const *events, float *ms);
 
+/* Direct pair sum without a plan and without any device allocation.  (The
+ * paper has no counterpart: this serves callers that cannot let a library
+ * allocate device memory, such as host codes whose device memory is owned
+ * by their own allocator or a fixed pool, and time loops that must never
+ * enter the CUDA allocator.)
+ *
+ * Computes what sg_solve computes for a plan created from `p` with
+ * method = SG_METHOD_DIRECT (p->method must say so): Phi, g_r, g_phi of each
+ * target fluid; any output may be NULL.  The scale-height fields
+ * p->H_g_field / p->H_d_field, when given, are read in place (device
+ * buffers in the dtype, kept alive by the caller until the work is done).
+ * SG_CHECK_FINITE is ignored.  Inputs and outputs are caller-owned device
+ * buffers as for sg_solve; the work is enqueued on `stream`.
+ *
+ * Scratch: the geometry tables live in one fixed 104 KiB array inside this
+ * library (every GPU that loads the library keeps it until the process
+ * exits), so grids are limited to nr <= 1024 and nphi <= 4096; larger grids
+ * return SG_ERR_UNSUPPORTED with a message on stderr.  The call allocates
+ * and frees nothing.  Its first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) for that device, so make that first
+ * call before any stream capture.  Every call shares the array and rewrites
+ * the part it reads before reading it; calls whose GPU work overlaps (two
+ * streams, two host threads) race on it, so serialise them.               */
+sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, const void *sigma_d,
+                            void *phi_g, void *gr_g, void *gphi_g,
+                            void *phi_d, void *gr_d, void *gphi_d, void *stream);
+
 /* Release a plan and all its device memory (NULL is a no-op).  Synchronises
  * the device before freeing.                                               */
 void sg_destroy(sg_plan *plan);

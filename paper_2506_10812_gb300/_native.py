@@ -21,7 +21,7 @@ SG_CHECK_FINITE = 2
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
-           "sg_solve_host", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_destroy", "sg_status_string",
+           "sg_solve_host", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_destroy", "sg_status_string",
            "sg_last_error")
 
 
@@ -72,6 +72,8 @@ def load() -> ctypes.CDLL:
     lib.sg_set_stage_events.restype = st
     lib.sg_stage_times.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_float)]
     lib.sg_stage_times.restype = st
+    lib.sg_direct_noalloc.argtypes = [ctypes.POINTER(SgParams)] + [vp] * 9
+    lib.sg_direct_noalloc.restype = st
     lib.sg_launches_per_solve.argtypes = [vp, u32]
     lib.sg_launches_per_solve.restype = i32
     lib.sg_destroy.argtypes = [vp]

@@ -14,6 +14,12 @@
 // for the nearest neighbours (no cancellation in r - r').
 #include <math.h>
 
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "sg.h"
 #include "sg_bessel.cuh"
 #include "sg_internal.h"
 
@@ -157,3 +163,139 @@ template cudaError_t launch_direct<double>(int, int, double, double, double, con
                                            const double *, unsigned int *, cudaStream_t);
 
 }  // namespace sg
+
+// ---------------------------------------------------------------------------
+// Allocation-free direct sum (sg_direct_noalloc in sg.h).
+//
+// Some callers cannot let a library allocate device memory: host codes whose
+// device memory is owned by their own allocator or a fixed pool (a library
+// cudaMalloc would bypass their accounting or fragment the pool), and time
+// loops that must never enter the CUDA allocator.  sg_direct_noalloc serves
+// them with the direct pair sum of a plan of the DIRECT method, without a
+// plan: the per-lag geometry tables that a plan keeps in its own device
+// memory live instead in the fixed array below, compiled into this library.
+// Every GPU that loads the library holds the array until the process exits.
+
+namespace {
+
+constexpr int kNoAllocMaxNr = 1024;     // largest nr the array can serve
+constexpr int kNoAllocMaxNphi = 4096;   // largest nphi
+// FP64 layout (FP32 uses the first half of each part):
+//   [0, 32768)       lag table over di: (sinh^2(D/2), expm1(D)), 2 (2 nr - 1) reals
+//   [32768, 98304)   lag table over dj: (sin^2(psi/2), sin psi), 2 nphi reals
+//   [98304, 106496)  cell-centre radii, nr reals
+constexpr size_t kNoAllocGeoJ = 32768, kNoAllocRcen = 98304, kNoAllocBytes = 106496;
+static_assert(2 * (2 * kNoAllocMaxNr - 1) * sizeof(double) <= kNoAllocGeoJ, "geo_i part too small");
+static_assert(2 * kNoAllocMaxNphi * sizeof(double) <= kNoAllocRcen - kNoAllocGeoJ, "geo_j part too small");
+static_assert(kNoAllocMaxNr * sizeof(double) <= kNoAllocBytes - kNoAllocRcen, "rcen part too small");
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_sg_noalloc_scratch[kNoAllocBytes];
+
+namespace sg {
+
+// Fill the three geometry tables for one grid (FP64 arithmetic).
+template <typename R>
+__global__ void k_direct_geometry(int nr, int nphi, double r_in, double du, R *geo_i, R *geo_j, R *rcen)
+{
+    const int n = max(2 * nr - 1, max(nphi, nr));
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        if (q < 2 * nr - 1) {
+            const double D = (q - (nr - 1)) * du, sh = sinh(0.5 * D);
+            geo_i[2 * q] = (R)(sh * sh);
+            geo_i[2 * q + 1] = (R)expm1(D);
+        }
+        if (q < nphi) {
+            const int jj = (2 * q <= nphi) ? q : nphi - q;
+            const double sg = (2 * q <= nphi) ? 1.0 : -1.0;
+            const double sp = sinpi((double)jj / nphi);
+            geo_j[2 * q] = (R)(sp * sp);
+            geo_j[2 * q + 1] = (R)(sg * sinpi(2.0 * jj / nphi));
+        }
+        if (q < nr) rcen[q] = (R)(r_in * exp((q + 0.5) * du));
+    }
+}
+
+}  // namespace sg
+
+namespace {
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the array for the current device, looked up once per
+// device (the first call on a device does the lookup).
+cudaError_t noalloc_scratch(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_sg_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+template <typename R>
+sg_status direct_noalloc_t(const sg_params *p, void *scratch, const void *sg_, const void *sd_,
+                           void *const outs[6], int nsrc, cudaStream_t s)
+{
+    const double du = std::log(p->r_out / p->r_in) / p->nr;
+    R *geo_i = (R *)scratch;
+    R *geo_j = (R *)((char *)scratch + kNoAllocGeoJ);
+    R *rcen = (R *)((char *)scratch + kNoAllocRcen);
+    // every entry the sum reads is rewritten here first, so nothing from an
+    // earlier call is used
+    const int n = std::max(2 * p->nr - 1, std::max(p->nphi, p->nr));
+    sg::k_direct_geometry<R><<<(n + 255) / 256, 256, 0, s>>>(p->nr, p->nphi, p->r_in, du, geo_i, geo_j, rcen);
+    cudaError_t e = cudaGetLastError();
+    for (int b = 0; b < nsrc && e == cudaSuccess; ++b) {
+        if (!(outs[3 * b] || outs[3 * b + 1] || outs[3 * b + 2])) continue;
+        e = sg::launch_direct<R>(p->nr, p->nphi, p->r_in, du, p->G, (const R *)sg_, nsrc == 2 ? (const R *)sd_ : nullptr,
+                                 (const R *)p->H_g_field, (const R *)p->H_d_field, p->h_g, p->h_d, b, (R *)outs[3 * b],
+                                 (R *)outs[3 * b + 1], (R *)outs[3 * b + 2], geo_i, geo_j, rcen, nullptr, s);
+    }
+    if (e != cudaSuccess) {
+        fprintf(stderr, "sg_direct_noalloc: %s\n", cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+    }
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, const void *sigma_d, void *phi_g,
+                                       void *gr_g, void *gphi_g, void *phi_d, void *gr_d, void *gphi_d, void *stream)
+{
+    if (!p || !sigma_g) return SG_ERR_ARG;
+    if (p->method != SG_METHOD_DIRECT || (p->dtype != SG_F32 && p->dtype != SG_F64)) return SG_ERR_ARG;
+    if (!(std::isfinite(p->r_in) && std::isfinite(p->r_out) && p->r_in > 0 && p->r_out > p->r_in) ||
+        !std::isfinite(p->G) || p->nr < 1 || p->nphi < 1)
+        return SG_ERR_ARG;
+    if (p->nr > kNoAllocMaxNr || p->nphi > kNoAllocMaxNphi) {
+        fprintf(stderr, "sg_direct_noalloc: grid %d x %d exceeds the fixed scratch (nr <= %d, nphi <= %d)\n", p->nr,
+                p->nphi, kNoAllocMaxNr, kNoAllocMaxNphi);
+        return SG_ERR_UNSUPPORTED;
+    }
+    if (!(p->h_g > 0 || p->H_g_field)) return SG_ERR_ARG;
+    const int nsrc = (p->h_d > 0 || p->H_d_field) ? 2 : 1;
+    if (nsrc == 2 && !sigma_d) return SG_ERR_ARG;
+    void *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "sg_direct_noalloc: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+        return SG_ERR_CUDA;
+    }
+    void *outs[6] = {phi_g, gr_g, gphi_g, phi_d, gr_d, gphi_d};
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->dtype == SG_F64 ? direct_noalloc_t<double>(p, scratch, sigma_g, sigma_d, outs, nsrc, s)
+                              : direct_noalloc_t<float>(p, scratch, sigma_g, sigma_d, outs, nsrc, s);
+}
+
