@@ -314,14 +314,40 @@ __device__ __forceinline__ void exchange_ct(T (&v)[16], int t, T *xb)
     for (int e = 0; e < 16; ++e) v[e] = rd[e * (TT + TT / 16)];
 }
 
+// Twiddles w_r = W^{r k}, r = 1..15, of one radix-16 butterfly: six table
+// loads (r = 1, 2, 3, 4, 8, 12), the other nine as one product of two loaded
+// values each (one extra rounding), which spares the L1 data path 9 loads.
+template <typename T>
+__device__ __forceinline__ void twiddles16(const T *__restrict__ p, int Ns, T (&w)[16])
+{
+    w[1] = __ldg(p);
+    w[2] = __ldg(p + Ns);
+    w[3] = __ldg(p + 2 * Ns);
+    w[4] = __ldg(p + 3 * Ns);
+    w[8] = __ldg(p + 7 * Ns);
+    w[12] = __ldg(p + 11 * Ns);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+    w[9] = cmul(w[8], w[1]);
+    w[10] = cmul(w[8], w[2]);
+    w[11] = cmul(w[8], w[3]);
+    w[13] = cmul(w[12], w[1]);
+    w[14] = cmul(w[12], w[2]);
+    w[15] = cmul(w[12], w[3]);
+}
+
 template <bool FWD, int L, int Ns, typename T>
 __device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *__restrict__ tp)
 {
     constexpr int TT = L / 16;
     if constexpr (Ns * 16 <= L) {
-        const T *p = tp + (t & (Ns - 1));
+        {
+            T w[16];
+            twiddles16(tp + (t & (Ns - 1)), Ns, w);
 #pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = twmul<FWD>(v[r], __ldg(p + (r - 1) * Ns));
+            for (int r = 1; r < 16; ++r) v[r] = twmul<FWD>(v[r], w[r]);
+        }
         dft16<FWD>(v);
         if constexpr (Ns * 16 < L) {
             exchange_ct<Ns, TT>(v, t, xb);
@@ -332,8 +358,20 @@ __device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *_
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const T *p = tp + ((t + TT * q) & (Ns - 1));
+            if constexpr (RL == 8) {
+                // w1..w4 loaded, w5..w7 = w4 w1..w3
+                T w[8];
 #pragma unroll
-            for (int r = 1; r < RL; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], __ldg(p + (r - 1) * Ns));
+                for (int r = 1; r <= 4; ++r) w[r] = __ldg(p + (r - 1) * Ns);
+                w[5] = cmul(w[4], w[1]);
+                w[6] = cmul(w[4], w[2]);
+                w[7] = cmul(w[4], w[3]);
+#pragma unroll
+                for (int r = 1; r < 8; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < RL; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], __ldg(p + (r - 1) * Ns));
+            }
         }
         if constexpr (RL == 2) {
 #pragma unroll

@@ -285,3 +285,21 @@ def test_errors_and_finite_check():
         assert e.value.status == N.SG_ERR_NONFINITE
         plan.solve(torch.ones((64, 128), device=dev))
         plan.sync()                       # flag cleared
+
+
+def test_column_pass_component_subsets_1024x2048():
+    """The FP32 column pass at the compile-time lengths stages one, two or
+    three kernel spectra (potential only, accelerations only, all): each
+    subset equals the fused solve exactly."""
+    d = inputs.lognormal_gas(1024, 2048, offset=7)
+    dev = torch.device("cuda:0")
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, None, G=d.G) as plan:
+        sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
+        full = plan.solve(sg)
+        pot = plan.potential(sg)
+        acc = plan.accel(sg)
+        only_r = plan.solve(sg, outputs=("gr",))
+        torch.cuda.synchronize()
+    assert torch.equal(pot["phi_g"], full["phi_g"])
+    assert torch.equal(acc["gr_g"], full["gr_g"]) and torch.equal(acc["gphi_g"], full["gphi_g"])
+    assert torch.equal(only_r["gr_g"], full["gr_g"])
