@@ -17,6 +17,7 @@ Two evaluations of the same finite sum are provided:
             square height", and Sec. 5.6 Eq. "grav. potential 2D", summed
             over all source cells (self cell excluded), in C with
             Kahan-compensated FP64 accumulation (``sg_oracle.c``).
+``indirect`` the indirect-term sums A, B of App. E (Sec. 5.4).
 ``fft64``   the paper's fast algorithm, Sec. 5.2 and App. C: the convolution
             kernels K_r, K_phi on the log-polar lattice, radial zero padding
             to 2 N_r, FP64 FFTs (numpy).  The potential uses the same
@@ -317,6 +318,36 @@ def fft64_apply(plan, sigma_g, sigma_d=None):
 def fft64(grid, sigma_g, sigma_d=None, h_g=0.05, h_d=None, G=1.0):
     """``fft64_apply(fft64_plan(...), ...)`` in one call."""
     return fft64_apply(fft64_plan(grid, h_g, h_d if sigma_d is not None else None, G), sigma_g, sigma_d)
+
+
+# --------------------------------------------------------------------------
+# Indirect term (Sec. 5.4, App. E)
+# --------------------------------------------------------------------------
+def indirect_kernel(d_a, H_a):
+    """App. E: K_a(d_a) = (1/sqrt(pi)) H_a^-2 (d_a/4) e^{d_a^2/4} [K1 - K0](d_a^2/4),
+    d_a = |r'| / H_a (note d^2/4, not the d^2/8 of the pair kernel)."""
+    d_a = np.asarray(d_a, dtype=np.float64)
+    H_a = np.asarray(H_a, dtype=np.float64)
+    _, D = k0e_D(d_a * d_a / 4.0)
+    return (1.0 / SQRT_PI) / (H_a * H_a) * (d_a / 4.0) * D
+
+
+def indirect(grid, sigma_g, sigma_d=None, h_g=None, h_d=None, H_g=None, H_d=None, G=1.0):
+    """App. E: A_a = sqrt(2) G sum_cells m_a K_a cos phi', B_a = the same with
+    sin phi', for each source fluid a (gas first), so that the gradient of
+    the indirect potential is (A cos phi + B sin phi) e_r +
+    (-A sin phi + B cos phi) e_phi with A = sum_a A_a, B = sum_a B_a.
+    Returns an array [[A_g, B_g], [A_d, B_d]] (one row for a gas-only disc)."""
+    R, P = grid.mesh()
+    out = []
+    srcs = [(sigma_g, _scale_height(grid, H_g, h_g))]
+    if sigma_d is not None:
+        srcs.append((sigma_d, _scale_height(grid, H_d, h_d)))
+    for sig, H in srcs:
+        m = _c64(sig) * R * R * grid.du * grid.dphi
+        w = np.sqrt(2.0) * G * m * indirect_kernel(R / H, H)
+        out.append([float(np.sum(w * np.cos(P))), float(np.sum(w * np.sin(P)))])
+    return np.array(out)
 
 
 # --------------------------------------------------------------------------

@@ -386,3 +386,37 @@ def test_exponential_disc_closed_form():
         errs.append(np.abs(out["gr_g"][sel, 0] - exact[sel]).max() / np.abs(exact).max())
     assert errs[1] < 2e-2, errs
     assert 1.8 < errs[0] / errs[1] < 2.3, errs
+
+
+# ---------------------------------------------------------- indirect term
+@pytest.mark.parametrize("rp,H", [(1.0, 0.05), (0.3, 0.1), (2.0, 0.5), (0.5, 0.02), (1.0, 1.0)])
+def test_indirect_kernel_is_the_vertical_integral(rp, H):
+    """App. E, Eq. "indirect term proof": the star's pull per unit surface
+    density of a Gaussian column at distance r', G int rho(z') r' /
+    (r'^2 + z'^2)^{3/2} dz', equals sqrt(2) K_a(r'/H) of Eq. "indirect term",
+    and equals (r'/sqrt(2 pi)) H^-3 F_1(d_a^2) with F_1 of App. A."""
+    f = lambda z: np.exp(-0.5 * (z / H) ** 2) / (np.sqrt(2 * np.pi) * H) * rp / (rp * rp + z * z) ** 1.5
+    pull = si.quad(f, -np.inf, np.inf, epsabs=0, epsrel=1e-12, limit=400)[0]
+    K = oracle.indirect_kernel(rp / H, H)
+    assert abs(np.sqrt(2) * K / pull - 1) < 1e-10
+    d2 = (rp / H) ** 2
+    F1 = si.quad(lambda t: np.exp(-t * t / 2) / (d2 + t * t) ** 1.5, -np.inf, np.inf, epsabs=0, epsrel=1e-12,
+                 limit=400)[0]
+    assert abs(np.sqrt(2) * K / (rp / np.sqrt(2 * np.pi) * H ** -3 * F1) - 1) < 1e-10
+
+
+def test_indirect_razor_thin_is_newtonian_star_pull():
+    """H -> 0: A = G sum m cos(phi') / r'^2, B = G sum m sin(phi') / r'^2 (the
+    star's acceleration towards the disc, Sec. 5.4)."""
+    g = oracle.Grid(16, 32, 0.5, 3.0)
+    rng = np.random.default_rng(31)
+    R, P = g.mesh()
+    sg = rng.uniform(0.5, 1.5, R.shape)
+    sd = rng.uniform(0.01, 0.02, R.shape)
+    ab = oracle.indirect(g, sg, sd, h_g=1e-6, h_d=1e-7, G=2.0)
+    for row, sig in zip(ab, (sg, sd)):
+        m = sig * R * R * g.du * g.dphi
+        ref = 2.0 * np.array([np.sum(m * np.cos(P) / R ** 2), np.sum(m * np.sin(P) / R ** 2)])
+        assert np.allclose(row, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
+    # an axisymmetric disc pulls the star nowhere
+    assert np.abs(oracle.indirect(g, 1.0 / R, h_g=0.05)).max() < 1e-12
