@@ -134,6 +134,19 @@ sg_status sg_solve(sg_plan *plan, const void *sigma_g, const void *sigma_d,
                    void *phi_g, void *gr_g, void *gphi_g,
                    void *phi_d, void *gr_d, void *gphi_d, void *stream);
 
+/* Indirect term (Sec. 5.4, App. E): the pull of each source fluid a on the
+ * central star, as the two sums
+ *     A_a = sqrt(2) G sum_cells m_a K_a cos phi',  B_a = sqrt(2) G sum_cells m_a K_a sin phi',
+ *     K_a = (1/sqrt(pi)) H_a^-2 (d_a/4) e^{d_a^2/4} [K1 - K0](d_a^2/4),  d_a = r'/H_a,
+ * with m_a = Sigma_a r'^2 du dphi and H_a = h_a r' (or the plan's
+ * scale-height field).  The indirect potential is
+ * Phi_ind = r (A cos phi + B sin phi) with A = sum_a A_a, B = sum_a B_a, and
+ * every fluid feels -grad Phi_ind = -(A cos phi + B sin phi) e_r +
+ * (A sin phi - B cos phi) e_phi.  ab_dev: device buffer of 2 nsrc doubles
+ * receiving (A_g, B_g[, A_d, B_d]), accumulated in FP64 in a fixed order
+ * (deterministic).  Both methods; asynchronous on `stream`.              */
+sg_status sg_indirect(sg_plan *plan, const void *sigma_g, const void *sigma_d, double *ab_dev, void *stream);
+
 /* sg_solve with HOST buffers: inputs and outputs are host memory (pinned
  * memory gives full copy bandwidth).  The call copies the inputs to
  * plan-owned device buffers, solves, copies the requested outputs back and

@@ -21,7 +21,7 @@ SG_CHECK_FINITE = 2
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
-           "sg_solve_host", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_destroy", "sg_status_string",
+           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_destroy", "sg_status_string",
            "sg_last_error")
 
 
@@ -66,6 +66,8 @@ def load() -> ctypes.CDLL:
     lib.sg_solve.restype = st
     lib.sg_solve_host.argtypes = [vp] * 10
     lib.sg_solve_host.restype = st
+    lib.sg_indirect.argtypes = [vp, vp, vp, vp, vp]
+    lib.sg_indirect.restype = st
     lib.sg_sync.argtypes = [vp, vp]
     lib.sg_sync.restype = st
     lib.sg_set_stage_events.argtypes = [vp, ctypes.POINTER(vp)]

@@ -29,6 +29,7 @@ struct sg_plan {
     void *rcen = nullptr, *geo_i = nullptr, *geo_j = nullptr;
     void *Hg = nullptr, *Hd = nullptr;
     unsigned int *flag = nullptr;         // bit 1: non-finite output, bit 2: staging timeout
+    double *ipart = nullptr;              // indirect-term partial sums
     void *stage = nullptr;                // sg_solve_host: [2 inputs + 6 outputs][cells]
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events
     char err[256] = {0};
@@ -63,7 +64,7 @@ void free_all(sg_plan *pl)
     if (pl->twp_col == pl->twp_col64) pl->twp_col = nullptr;
     void *ptrs[] = {pl->tw_row, pl->tw_row64, pl->twp_row, pl->twp_row64, pl->twp_col, pl->twp_col64,
                     pl->tab, pl->sh, pl->oh, pl->rcen, pl->geo_i, pl->geo_j, pl->Hg, pl->Hd, pl->flag,
-                    pl->stage};
+                    pl->stage, pl->ipart};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     // leave no error state behind for the next call's launch check
@@ -364,6 +365,7 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
     if (pl->f64) SG_TRY(upload(&pl->rcen, centres<double>(p->nr, p->r_in, pl->du), s), "centres");
     else SG_TRY(upload(&pl->rcen, centres<float>(p->nr, p->r_in, pl->du), s), "centres");
     SG_TRY(cudaMalloc((void **)&pl->flag, sizeof(unsigned int)), "flag");
+    SG_TRY(cudaMalloc((void **)&pl->ipart, (size_t)indirect_blocks(p->nphi) * 4 * sizeof(double)), "indirect sums");
     SG_TRY(cudaMemsetAsync(pl->flag, 0, sizeof(unsigned int), s), "flag");
     if (fft) {
         SG_TRY(upload(&pl->tw_row64, twiddles<double>(p->nphi), s), "twiddles");
@@ -496,6 +498,26 @@ sg_status sg_solve_host(sg_plan *pl, const void *sigma_g, const void *sigma_d, v
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(pl, e, "solve");
+    return SG_OK;
+}
+
+sg_status sg_indirect(sg_plan *pl, const void *sigma_g, const void *sigma_d, double *ab_dev, void *stream)
+{
+    if (!pl) return SG_ERR_ARG;
+    sg_status st = check_device(pl);
+    if (st != SG_OK) return st;
+    if (!sigma_g || !ab_dev) return fail(pl, SG_ERR_ARG, "sigma_g and ab_dev are required");
+    if (pl->nsrc == 2 && !sigma_d) return fail(pl, SG_ERR_ARG, "bi-fluid plan needs sigma_d");
+    const int nr = pl->p.nr, nphi = pl->p.nphi;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e =
+        pl->f64 ? launch_indirect<double>(nr, nphi, pl->nsrc, (const double *)sigma_g, (const double *)sigma_d,
+                                          (const double *)pl->Hg, (const double *)pl->Hd, pl->p.h_g, pl->p.h_d,
+                                          (const double *)pl->rcen, pl->p.G, pl->du, pl->dphi, pl->ipart, ab_dev, s)
+                : launch_indirect<float>(nr, nphi, pl->nsrc, (const float *)sigma_g, (const float *)sigma_d,
+                                         (const float *)pl->Hg, (const float *)pl->Hd, pl->p.h_g, pl->p.h_d,
+                                         (const float *)pl->rcen, pl->p.G, pl->du, pl->dphi, pl->ipart, ab_dev, s);
+    if (e != cudaSuccess) return cuda_fail(pl, e, "indirect term");
     return SG_OK;
 }
 

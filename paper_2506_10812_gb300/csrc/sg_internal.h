@@ -68,6 +68,14 @@ template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
                             const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s);
 
+// Indirect term (App. E): out[2 a + {0, 1}] = (A_a, B_a) in FP64; partial
+// holds indirect_blocks(nphi) x 4 doubles.
+int indirect_blocks(int nphi);
+template <typename R>
+cudaError_t launch_indirect(int nr, int nphi, int nsrc, const R *s0, const R *s1, const R *H0, const R *H1,
+                            double h0, double h1, const R *rcen, double G, double du, double dphi, double *partial,
+                            double *out, cudaStream_t s);
+
 // Direct pair sum (general scale heights) for one target fluid.
 template <typename R>
 cudaError_t launch_direct(int nr, int nphi, double r_in, double du, double G, const R *sig_g,

@@ -136,6 +136,16 @@ class Plan:
         N.check(st, self._h, "sg_accel")
         return res
 
+    def indirect(self, sigma_g, sigma_d=None):
+        """Indirect-term sums (App. E) per source fluid: float64 tensor
+        [[A_g, B_g], ([A_d, B_d])] on the plan's device."""
+        sigma_g, sigma_d = self._inputs(sigma_g, sigma_d)
+        out = torch.empty((2 if self.bifluid else 1, 2), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            st = self._lib.sg_indirect(self._h, _ptr(sigma_g), _ptr(sigma_d), _ptr(out), self._stream())
+        N.check(st, self._h, "sg_indirect")
+        return out
+
     def kernel_table(self, pair=N.SG_PAIR_GG, comp=N.SG_COMP_R):
         """Real-space lattice kernel [2 nr, nphi] of one ordered pair (App. C)."""
         out = torch.empty((2 * self.nr, self.nphi), dtype=self.dtype, device=self.device)

@@ -303,3 +303,31 @@ def test_column_pass_component_subsets_1024x2048():
     assert torch.equal(pot["phi_g"], full["phi_g"])
     assert torch.equal(acc["gr_g"], full["gr_g"]) and torch.equal(acc["gphi_g"], full["gphi_g"])
     assert torch.equal(only_r["gr_g"], full["gr_g"])
+
+
+# ---------------------------------------------------------- indirect term
+@pytest.mark.parametrize("nr,nphi,bif,dtype,method", [
+    (64, 128, False, torch.float64, "fft"), (256, 512, True, torch.float32, "fft"),
+    (2048, 4096, False, torch.float32, "fft"), (24, 40, True, torch.float64, "direct")])
+def test_indirect_term_vs_oracle(nr, nphi, bif, dtype, method):
+    """App. E sums A_a, B_a against the oracle (FP64 accumulation on both
+    sides; the direct plan uses position-dependent scale heights)."""
+    d = rounded(inputs.ragged_noise(nr, nphi, bifluid=bif), dtype)
+    dev = torch.device("cuda:0")
+    Hg = Hd = None
+    if method == "direct":
+        rng = np.random.default_rng(41)
+        R, _ = grid(d).mesh()
+        Hg = R * rng.uniform(0.03, 0.1, R.shape)
+        Hd = R * rng.uniform(0.002, 0.02, R.shape)
+    ref = oracle.indirect(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, H_g=Hg, H_d=Hd, G=d.G)
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, dtype=dtype, method=method,
+             H_g=None if Hg is None else torch.tensor(Hg, dtype=dtype, device=dev),
+             H_d=None if Hd is None else torch.tensor(Hd, dtype=dtype, device=dev)) as plan:
+        sg = torch.tensor(d.sigma_g, dtype=dtype, device=dev)
+        sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=dtype, device=dev)
+        ab = plan.indirect(sg, sd).cpu().numpy()
+    assert ab.shape == ref.shape
+    scale = np.abs(ref).max()
+    tol = 1e-12 if method == "fft" or dtype == torch.float64 else 1e-6
+    assert np.abs(ab - ref).max() <= tol * scale, (ab, ref)
