@@ -54,6 +54,7 @@ extern "C" {
 #endif
 
 typedef struct sg_plan sg_plan;
+typedef struct sg_batch sg_batch;
 
 typedef enum {
     SG_OK = 0,
@@ -63,7 +64,7 @@ typedef enum {
     SG_ERR_CUDA = 4,               /* a CUDA runtime call or launch failed          */
     SG_ERR_OOM = 5,                /* device allocation failed                      */
     SG_ERR_NONFINITE = 6,          /* SG_CHECK_FINITE found a NaN/Inf output         */
-    SG_ERR_TIMEOUT = 7             /* reserved                                       */
+    SG_ERR_TIMEOUT = 7             /* a bounded device-side wait gave up            */
 } sg_status;
 
 enum { SG_F32 = 0, SG_F64 = 1 };                  /* plan dtype                        */
@@ -205,6 +206,96 @@ sg_status sg_stage_times(void *const *events, float *ms);
 sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, const void *sigma_d,
                             void *phi_g, void *gr_g, void *gphi_g,
                             void *phi_d, void *gr_d, void *gphi_d, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batches of independent discs.  The paper evolves one disc per run and
+ * builds its kernel once per run (Sec. 5.2); a batch binds many FFT plans
+ * (uneven grids, gas-only or gas + dust, one dtype, one device) and their
+ * device buffers, and solves all of them with ONE persistent kernel launch.
+ * That launch works through a task list: for every disc the row transforms of
+ * each source, the column pass, and the inverse row transforms of each output.
+ * Blocks take tasks in list order from a device counter.  A task that depends
+ * on a disc's earlier stage waits, on the device, for that stage's
+ * completion count.  The list is ordered so that every wait is on tasks
+ * taken before it, and each wait is bounded in time.  The
+ * counter reset and the launch are captured once in a CUDA graph, so
+ * sg_batch_solve is one graph launch.
+ *
+ * Results are those of sg_solve on each plan with the same buffers: the
+ * same transforms and products in the same order, bit-identical except that
+ * sg_solve's FP32 transforms of length 2048 and 4096 derive 9 of the 15
+ * twiddles of each radix-16 pass as products of loaded ones (one extra
+ * rounding), where the batch loads all of them.  Results do not depend on
+ * the launch configuration (threads, blocks, task order).
+ * ---------------------------------------------------------------------- */
+#define SG_BATCH_HOST_GATE 4u   /* opts flag: blocks wait for sg_batch_release      */
+
+enum { SG_BATCH_ORDER_PIPELINED = 0, SG_BATCH_ORDER_STAGED = 1 };
+
+typedef struct {
+    int32_t threads;       /* threads per block, 256 or 512 (0: 256)                 */
+    int32_t ctas_per_sm;   /* resident blocks per SM of the persistent grid
+                              (0: the occupancy maximum; larger values are capped)   */
+    int32_t order;         /* task order: SG_BATCH_ORDER_PIPELINED interleaves the
+                              stages of consecutive discs (disc k's rows, k-1's
+                              columns, k-2's inverse rows); _STAGED runs every
+                              disc's stage s before any stage s+1               */
+    int32_t autotune;      /* 1: time every (threads, ctas_per_sm, order)
+                              candidate on the bound buffers at create and keep
+                              the fastest; threads/ctas_per_sm/order are ignored   */
+    uint32_t flags;        /* SG_CHECK_FINITE, SG_BATCH_HOST_GATE                   */
+    double timeout_ms;     /* bound of each device-side wait (0: 2000 ms)          */
+} sg_batch_opts;
+
+/* Bind `n` FFT plans and their buffers into a batch.  For disc k:
+ * sigma_g[k], sigma_d[k] (NULL for a gas-only plan) are its inputs and
+ * outs[6 k + q] its outputs in sg_solve order (phi_g, gr_g, gphi_g, phi_d,
+ * gr_d, gphi_d; NULL skips one; the dust outputs of a gas-only plan must be
+ * NULL), all caller-owned device buffers that must stay valid, at the same
+ * addresses, for the batch's lifetime (the graph holds the addresses; write
+ * each step's inputs into the same buffers).  Every plan keeps owning its
+ * kernel spectra and scratch, and must outlive the batch and not be solved on
+ * another stream while a batch solve runs.  opts may be NULL (defaults).
+ * With opts->autotune the call runs the batch several times on `stream`
+ * (outputs are overwritten).  Synchronises `stream`.  Errors: SG_ERR_ARG
+ * (NULL, n < 1, mixed dtypes or devices, a direct-method plan, missing
+ * sigma_d), SG_ERR_UNSUPPORTED (a transform longer than 16 x threads:
+ * nphi > 8192 or nr > 2048 with 256 threads), SG_ERR_OOM, SG_ERR_CUDA.    */
+sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n,
+                          const void *const *sigma_g, const void *const *sigma_d,
+                          void *const *outs, const sg_batch_opts *opts, void *stream);
+
+/* Solve every disc of the batch: one graph launch (a 4-byte-per-disc
+ * counter reset and the persistent kernel) on `stream`.  Never synchronises
+ * the host.  With SG_BATCH_HOST_GATE every block first waits (bounded by
+ * timeout_ms) until sg_batch_release is called; each gated solve must then
+ * be followed by sg_batch_release and sg_batch_sync before the next.      */
+sg_status sg_batch_solve(sg_batch *batch, void *stream);
+
+/* The per-disc baseline: sg_solve on every plan in turn (three launches per
+ * disc), same buffers, same results.                                     */
+sg_status sg_batch_solve_loop(sg_batch *batch, void *stream);
+
+/* Open the host gate of a SG_BATCH_HOST_GATE batch (a store to mapped host
+ * memory that the blocks poll); SG_ERR_ARG for a batch without the gate.  */
+sg_status sg_batch_release(sg_batch *batch);
+
+/* Synchronise `stream` and report: SG_ERR_TIMEOUT if a device-side wait of
+ * a solve since the last sg_batch_sync gave up (its outputs are incomplete;
+ * the context stays usable), SG_ERR_NONFINITE (SG_CHECK_FINITE) if an output
+ * held a NaN or Inf, SG_ERR_CUDA on an asynchronous error.  Clears the
+ * flags.                                                                 */
+sg_status sg_batch_sync(sg_batch *batch, void *stream);
+
+/* The configuration in use (threads, ctas_per_sm, order; autotune = 1 if it
+ * was tuned), the persistent grid size, the number of tasks and the tuned
+ * time per solve in ms (0 when not tuned); any pointer may be NULL.       */
+sg_status sg_batch_config(const sg_batch *batch, sg_batch_opts *opts, int32_t *grid,
+                          int32_t *ntasks, float *tuned_ms);
+
+/* Release the batch (not its plans or buffers).  Synchronises the device. */
+void sg_batch_destroy(sg_batch *batch);
+const char *sg_batch_last_error(const sg_batch *batch);
 
 /* Release a plan and all its device memory (NULL is a no-op).  Synchronises
  * the device before freeing.                                               */

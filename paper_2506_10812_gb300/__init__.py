@@ -11,13 +11,15 @@ package only marshals torch tensors into it.  ``inputs`` draws seeded
 synthetic discs and can be imported without the CUDA library.
 """
 
-__all__ = ["Plan", "inputs"]
+__all__ = ["Plan", "Batch", "inputs"]
 
 
 def __getattr__(name):
     import importlib
     if name == "Plan":
         return importlib.import_module(".plan", __name__).Plan
+    if name == "Batch":
+        return importlib.import_module(".batch", __name__).Batch
     if name in ("inputs", "build"):
         return importlib.import_module("." + name, __name__)
     raise AttributeError(name)

@@ -18,11 +18,14 @@ SG_METHOD_FFT, SG_METHOD_DIRECT = 0, 1
 SG_PAIR_GG, SG_PAIR_GD, SG_PAIR_DG, SG_PAIR_DD = 0, 1, 2, 3
 SG_COMP_PHI, SG_COMP_R, SG_COMP_AZ = 0, 1, 2
 SG_CHECK_FINITE = 2
+SG_BATCH_HOST_GATE = 4
+SG_BATCH_ORDER_PIPELINED, SG_BATCH_ORDER_STAGED = 0, 1
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
-           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_destroy", "sg_status_string",
-           "sg_last_error")
+           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_batch_create", "sg_batch_solve",
+           "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_destroy",
+           "sg_batch_last_error", "sg_destroy", "sg_status_string", "sg_last_error")
 
 
 class SgParams(ctypes.Structure):
@@ -32,6 +35,11 @@ class SgParams(ctypes.Structure):
                 ("H_g_field", ctypes.c_void_p), ("H_d_field", ctypes.c_void_p),
                 ("G", ctypes.c_double), ("dtype", ctypes.c_int32), ("method", ctypes.c_int32),
                 ("flags", ctypes.c_uint32)]
+
+
+class SgBatchOpts(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("flags", ctypes.c_uint32), ("timeout_ms", ctypes.c_double)]
 
 
 class SgError(RuntimeError):
@@ -76,6 +84,21 @@ def load() -> ctypes.CDLL:
     lib.sg_stage_times.restype = st
     lib.sg_direct_noalloc.argtypes = [ctypes.POINTER(SgParams)] + [vp] * 9
     lib.sg_direct_noalloc.restype = st
+    lib.sg_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(SgBatchOpts), vp]
+    lib.sg_batch_create.restype = st
+    for name in ("sg_batch_solve", "sg_batch_solve_loop", "sg_batch_sync"):
+        getattr(lib, name).argtypes = [vp, vp]
+        getattr(lib, name).restype = st
+    lib.sg_batch_release.argtypes = [vp]
+    lib.sg_batch_release.restype = st
+    lib.sg_batch_config.argtypes = [vp, ctypes.POINTER(SgBatchOpts), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                    ctypes.POINTER(ctypes.c_float)]
+    lib.sg_batch_config.restype = st
+    lib.sg_batch_destroy.argtypes = [vp]
+    lib.sg_batch_destroy.restype = None
+    lib.sg_batch_last_error.argtypes = [vp]
+    lib.sg_batch_last_error.restype = ctypes.c_char_p
     lib.sg_launches_per_solve.argtypes = [vp, u32]
     lib.sg_launches_per_solve.restype = i32
     lib.sg_destroy.argtypes = [vp]
@@ -88,13 +111,13 @@ def load() -> ctypes.CDLL:
     return lib
 
 
-def check(status: int, plan_handle=None, what: str = "sg call") -> None:
+def check(status: int, plan_handle=None, what: str = "sg call", batch_handle=None) -> None:
     if status == SG_OK:
         return
     lib = load()
     msg = lib.sg_status_string(status).decode()
-    if plan_handle:
-        detail = lib.sg_last_error(plan_handle).decode()
+    if plan_handle or batch_handle:
+        detail = (lib.sg_batch_last_error(batch_handle) if batch_handle else lib.sg_last_error(plan_handle)).decode()
         if detail:
             msg = f"{msg}: {detail}"
     raise SgError(status, f"{what}: {msg}")

@@ -14,27 +14,6 @@
 
 using namespace sg;
 
-struct sg_plan {
-    sg_params p{};
-    int nsrc = 1;
-    bool f64 = false;
-    int L = 0, N = 0;
-    double du = 0, dphi = 0;
-    int device = 0;
-    size_t esz = 4;                       // bytes per real element
-    void *tw_row = nullptr, *tw_row64 = nullptr;     // exp(-2 pi i k / nphi), k < nphi
-    void *twp_row = nullptr, *twp_row64 = nullptr;   // per-pass tables, length nphi / 2
-    void *twp_col = nullptr, *twp_col64 = nullptr;   // per-pass tables, length 2 nr
-    void *tab = nullptr, *sh = nullptr, *oh = nullptr;
-    void *rcen = nullptr, *geo_i = nullptr, *geo_j = nullptr;
-    void *Hg = nullptr, *Hd = nullptr;
-    unsigned int *flag = nullptr;         // bit 1: non-finite output, bit 2: staging timeout
-    double *ipart = nullptr;              // indirect-term partial sums
-    void *stage = nullptr;                // sg_solve_host: [2 inputs + 6 outputs][cells]
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events
-    char err[256] = {0};
-};
-
 namespace {
 
 sg_status fail(sg_plan *pl, sg_status s, const char *fmt, ...)

@@ -1,0 +1,857 @@
+// Many independent discs in one persistent launch (the paper evolves one
+// disc per run and precomputes its kernel once, Sec. 5.2; here a batch of
+// FFT plans, uneven grids, gas-only or gas + dust, is solved together).
+//
+// Work decomposition.  A disc's FFT solve has three stages (the arithmetic is
+// that of sg_kernels.cu, see its header): row R2C of every source, the
+// column pass (forward padded FFT, products with the kernel spectra, inverse
+// FFT of every requested output), and the row C2R + epilogue of every
+// output.  Each stage is cut into tasks that fill one block: a block of
+// `threads` threads runs G = threads / T transforms side by side, T = n / 16
+// threads per length-n transform, so a task is G rows (or G columns) of one
+// disc.  The host writes the task list once; blocks of the persistent grid
+// take tasks in list order from a device counter.  A column task of disc d
+// waits until every row task of d has finished; an inverse-row task waits for
+// every column task of d.  The list puts every task after the tasks it waits
+// for, and a block takes a task only after it has finished its previous one,
+// so every awaited task is held by a running block: the waits cannot form a
+// cycle, whatever the number of resident blocks.  Each wait is bounded
+// (%globaltimer), sets bit 2 of the batch flag and aborts the launch when it
+// gives up.
+//
+// Memory ordering: a finished task's threads fence (gpu scope), the block
+// synchronises, and one thread increments the disc's stage counter; the
+// waiting thread reads the counter with ld.acquire.gpu and its block
+// synchronises before reading.  Data written during the launch (the spectral
+// intermediates) is read with ld.global.cg, never through the non-coherent
+// path; the kernel spectra, twiddles and inputs are read-only.
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sg.h"
+#include "sg_fft.cuh"
+#include "sg_internal.h"
+#include "sg_mem.cuh"
+
+namespace sg {
+
+enum { TASK_FWD = 0, TASK_COL0 = 1, TASK_COL = 2, TASK_INV = 3 };
+
+template <typename R>
+struct BatchDisc {
+    const R *s[2];                 // sources [nr][nphi]
+    cplx<R> *sh;                   // row spectra, [nsrc][N][nr] column-blocked
+    const cplx<R> *tab;            // kernel spectra of the plan
+    cplx<R> *oh;                   // column-pass output, [6][N][nr] column-blocked
+    R *out[6];                     // outputs by slot 3 b + c (NULL: not requested)
+    const R *rcen;                 // r_i
+    const cplx<R> *tw_row, *twp_row, *twp_col;
+    int nr, nphi, nsrc;
+    uint32_t outmask;
+    unsigned n_fwd, n_col;         // tasks of stage 0 and 1 (the wait targets)
+};
+
+struct BatchArgs {
+    const int4 *tasks;             // {type, disc, a (source) or q (slot), tile}
+    int ntasks;
+    int ndisc;
+    unsigned *ctl;                 // [0] next task, [1] abort, [2..] fwd_done[ndisc], col_done[ndisc]
+    unsigned *flag;                // bit 1: non-finite output, bit 2: a wait gave up
+    int check_finite;
+    const unsigned *gate;          // mapped host word, or NULL
+    unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait (one thread) until *p >= target.  Gives up after timeout_ns
+// of %globaltimer time or 2^25 polls, or when another block has aborted;
+// the first to give up sets flag bit 2 and the abort word.
+__device__ bool wait_at_least(const unsigned *p, unsigned target, bool sys, const BatchArgs &a)
+{
+    auto rd = [&]() { return sys ? ld_acquire_sys(p) : ld_acquire_gpu(p); };
+    if (rd() >= target) return true;
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 32;
+    for (int it = 0; it < (1 << 25); ++it) {
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+        if (rd() >= target) return true;
+        if (ld_acquire_gpu(a.ctl + 1)) return false;
+        if (global_ns() - t0 > a.timeout_ns) break;
+    }
+    atomicOr(a.flag, 4u);
+    atomicExch(a.ctl + 1, 1u);
+    return false;
+}
+
+// ------------------------------------------------------------ row R2C task
+// Rows rb G .. rb G + G - 1 of source `a` (rows past nr recompute row nr - 1
+// and store nothing).  Same arithmetic as k_rows_fwd.
+template <typename R>
+__device__ void task_fwd(const BatchDisc<R> &D, int a, int rb, unsigned char *smem)
+{
+    using C = cplx<R>;
+    R *red = reinterpret_cast<R *>(smem);
+    C *sm = reinterpret_cast<C *>(smem + 64 * sizeof(double));
+    const int nr = D.nr, nphi = D.nphi, N = nphi >> 1, T = N >> 4;
+    const int G = blockDim.x / T, lg = __ffs(G) - 1;
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    const int i0 = rb * G, iv = min(i0 + g, nr - 1);
+    const C *xr = reinterpret_cast<const C *>(D.s[a] + (size_t)iv * nphi);
+    C *xb = sm + g * padded_len(N);
+    C v[16];
+    const R sc = D.rcen[iv];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const C z = __ldg(xr + t + T * e);
+        v[e] = mkc<C>(z.x * sc, z.y * sc);
+    }
+    R s = 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) s += v[e].x + v[e].y;
+    const int seg = T < 32 ? T : 32;
+    for (int o = seg >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (T > 32) {
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        s = 0;
+        const int w0 = (g * T) >> 5, nw = T >> 5;
+        for (int w = 0; w < nw; ++w) s += red[w0 + w];
+    }
+    const R mean = s / (R)nphi;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = mkc<C>(v[e].x - mean, v[e].y - mean);
+    fft_reg<true>(v, N, T, t, xb, D.twp_row);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) xb[pidx(t + T * e)] = v[e];
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int k = t + T * e;
+        const C Z = v[e];
+        if (k == 0) {
+            v[e] = mkc<C>(Z.x + Z.y + mean * (R)nphi, Z.x - Z.y);
+        } else {
+            const C Zc = cconj(xb[pidx(N - k)]);
+            const C E = cscale(cadd(Z, Zc), (R)0.5);
+            const C O = cscale(cmul_mi(csub(Z, Zc)), (R)0.5);
+            v[e] = cadd(E, cmul(O, __ldg(&D.tw_row[k])));
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) sm[tile_idx_g<C>(t + T * e, g, lg)] = v[e];
+    __syncthreads();
+    C *out = D.sh + (size_t)a * N * nr;
+    const int per = G * BW;
+    const uint64_t pl = l2_evict_last();
+    for (int idx = threadIdx.x; idx < N * G; idx += blockDim.x) {
+        const int bb = idx / per, rem = idx - bb * per;
+        const int gg = rem / BW, c = rem - gg * BW;
+        if (i0 + gg < nr)
+            st_hint(out + ((size_t)bb * nr + i0 + gg) * BW + c, sm[tile_idx_g<C>(bb * BW + c, gg, lg)], pl);
+    }
+}
+
+// ----------------------------------------------------------- column tasks
+template <typename C>
+__device__ __forceinline__ C tab_at(const C *col, int k, int H, bool upper, uint64_t pol)
+{
+    return upper ? cconj(ld_hint(col + 2 * H - k, pol)) : ld_hint(col + k, pol);
+}
+
+// Columns cb G + g (1 <= m < N; other groups recompute column N - 1 or 1 and
+// store nothing).  Same arithmetic as k_cols.
+template <typename R, int NS>
+__device__ void task_col(const BatchDisc<R> &D, int cb, unsigned char *smem)
+{
+    using C = cplx<R>;
+    const int nr = D.nr, N = D.nphi >> 1, L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
+    const int G = blockDim.x / T;
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    const int m = cb * G + g;
+    const bool valid = m >= 1 && m < N;
+    const int mv = min(max(m, 1), N - 1);
+    C *xb = reinterpret_cast<C *>(smem) + (size_t)g * (padded_len(L) + (NS - 1) * 2 * L);
+    C *sspec = xb + padded_len(L);                 // NS == 2: both spectra, own entries only
+    const uint64_t pf = l2_evict_first();
+    C v[16];
+    C spec[NS == 1 ? 16 : 1];
+#pragma unroll 1
+    for (int a = 0; a < NS; ++a) {
+        const C *src = D.sh + (size_t)a * N * nr;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(src + blk(mv, t + T * e, nr), pf);
+#pragma unroll
+        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
+        fft_reg<true>(v, L, T, t, xb, D.twp_col);
+        if constexpr (NS == 1) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) spec[e] = v[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) sspec[a * L + t + T * e] = v[e];
+        }
+    }
+    const uint64_t pl = l2_evict_last();
+#pragma unroll 1
+    for (int q = 0; q < 3 * NS; ++q) {
+        if (!((D.outmask >> q) & 1u)) continue;
+        const int b = q / 3, c = q - 3 * b;
+        const C *tc[NS];
+#pragma unroll
+        for (int a = 0; a < NS; ++a) tc[a] = D.tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1) + mv) * P;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int k = t + T * e;
+            C acc = mkc<C>(0, 0);
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                C S = tab_at(tc[a], k, H, e >= 8, pf);
+                if (c == 2) S = cmul_mi(S);
+                C Z;
+                if constexpr (NS == 1) Z = spec[e];
+                else Z = sspec[a * L + k];
+                acc = cfma(Z, S, acc);
+            }
+            v[e] = acc;
+        }
+        fft_reg<false>(v, L, T, t, xb, D.twp_col);
+        if (valid) {
+            C *o = D.oh + (size_t)q * N * nr;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) st_hint(o + blk(m, t + T * e, nr), v[e], pl);
+        }
+    }
+}
+
+// Column m = 0 (the packed m = 0 and m = nphi/2 real columns).  Every group
+// computes it; group 0 stores.  Same arithmetic as col0_path.
+template <typename R, int NS>
+__device__ void task_col0(const BatchDisc<R> &D, unsigned char *smem)
+{
+    using C = cplx<R>;
+    const int nr = D.nr, N = D.nphi >> 1, L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    C *xb = reinterpret_cast<C *>(smem) + (size_t)g * (padded_len(L) + 2 * L);
+    C *spec = xb + padded_len(L);
+    C v[16];
+    for (int a = 0; a < NS; ++a) {
+        const C *col = D.sh + (size_t)a * N * nr;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(col + blk(0, t + T * e, nr), l2_evict_first());
+#pragma unroll
+        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
+        fft_reg<true>(v, L, T, t, xb, D.twp_col);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) spec[a * L + t + T * e] = v[e];
+    }
+    __syncthreads();
+    for (int q = 0; q < 3 * NS; ++q) {
+        if (!((D.outmask >> q) & 1u)) continue;
+        const int b = q / 3, c = q - 3 * b;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int k = t + T * e;
+            C acc = mkc<C>(0, 0);
+            for (int a = 0; a < NS; ++a) {
+                const C *t0 = D.tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1)) * P;
+                const C *tn = t0 + (size_t)N * P;
+                const C Z = spec[a * L + k];
+                const C Zm = cconj(spec[a * L + ((L - k) & (L - 1))]);
+                C S0 = e >= 8 ? cconj(t0[2 * H - k]) : t0[k];
+                C SN = e >= 8 ? cconj(tn[2 * H - k]) : tn[k];
+                if (c == 2) {
+                    S0 = cmul_mi(S0);
+                    SN = cmul_mi(SN);
+                }
+                acc = cadd(acc, cscale(cadd(cmul(cadd(Z, Zm), S0), cmul(csub(Z, Zm), SN)), (R)0.5));
+            }
+            v[e] = acc;
+        }
+        fft_reg<false>(v, L, T, t, xb, D.twp_col);
+        if (g == 0) {
+            C *o = D.oh + (size_t)q * N * nr;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) o[blk(0, t + T * e, nr)] = v[e];
+        }
+    }
+}
+
+// ------------------------------------------------- row C2R + epilogue task
+// Rows rb G .. of output slot q.  Same arithmetic as k_rows_inv.
+template <typename R>
+__device__ void task_inv(const BatchDisc<R> &D, int q, int rb, const BatchArgs &A, unsigned char *smem)
+{
+    using C = cplx<R>;
+    C *sm = reinterpret_cast<C *>(smem + 64 * sizeof(double));
+    const int nr = D.nr, nphi = D.nphi, N = nphi >> 1, T = N >> 4;
+    const int G = blockDim.x / T, lg = __ffs(G) - 1;
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    const int i0 = rb * G;
+    const C *src = D.oh + (size_t)q * N * nr;
+    const int per = G * BW;
+    {
+        // N G = 16 blockDim elements: 16 loads per thread, all issued first
+        const uint64_t pf = l2_evict_first();
+        C tmp[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int idx = threadIdx.x + j * blockDim.x;
+            const int bb = idx / per, rem = idx - bb * per;
+            const int gg = rem / BW, c = rem - gg * BW;
+            const int row = min(i0 + gg, nr - 1);
+            tmp[j] = ld_cg_hint(src + ((size_t)bb * nr + row) * BW + c, pf);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int idx = threadIdx.x + j * blockDim.x;
+            const int bb = idx / per, rem = idx - bb * per;
+            const int gg = rem / BW, c = rem - gg * BW;
+            sm[tile_idx_g<C>(bb * BW + c, gg, lg)] = tmp[j];
+        }
+    }
+    __syncthreads();
+    C v[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int k = t + T * e;
+        const C X = sm[tile_idx_g<C>(k, g, lg)];
+        if (k == 0) {
+            v[e] = mkc<C>(X.x + X.y, X.x - X.y);
+        } else {
+            const C Xc = cconj(sm[tile_idx_g<C>(N - k, g, lg)]);
+            v[e] = cadd(cadd(X, Xc), cmul_i(cmulc(csub(X, Xc), __ldg(&D.tw_row[k]))));
+        }
+    }
+    fft_reg<false>(v, N, T, t, sm + g * padded_len(N), D.twp_row);
+    const int i = i0 + g;
+    if (i < nr) {
+        const R sc = (q % 3) == 0 ? (R)1 : (R)1 / D.rcen[i];
+        C *out = reinterpret_cast<C *>(D.out[q] + (size_t)i * nphi);
+        bool bad = false;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const C y = mkc<C>(v[e].x * sc, v[e].y * sc);
+            bad |= !(isfinite(y.x) && isfinite(y.y));
+            out[t + T * e] = y;
+        }
+        if (A.check_finite && bad) atomicOr(A.flag, 1u);
+    }
+}
+
+// ------------------------------------------------------- persistent kernel
+template <typename R>
+__global__ void __launch_bounds__(512) k_batch(const BatchDisc<R> *__restrict__ discs, const __grid_constant__ BatchArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int4 s_task;
+    unsigned *next = A.ctl, *fwd_done = A.ctl + 2, *col_done = A.ctl + 2 + A.ndisc;
+    if (A.gate) {
+        if (threadIdx.x == 0) s_task.x = wait_at_least(A.gate, 1u, true, A) ? 0 : -1;
+        __syncthreads();
+        if (s_task.x < 0) return;
+    }
+    for (;;) {
+        __syncthreads();                        // every thread has read the previous s_task
+        if (threadIdx.x == 0) {
+            int4 tk = make_int4(-1, 0, 0, 0);
+            if (!ld_acquire_gpu(A.ctl + 1)) {
+                const unsigned i = atomicAdd(next, 1u);
+                if (i < (unsigned)A.ntasks) tk = A.tasks[i];
+            }
+            if (tk.x == TASK_COL0 || tk.x == TASK_COL) {
+                if (!wait_at_least(fwd_done + tk.y, discs[tk.y].n_fwd, false, A)) tk.x = -1;
+            } else if (tk.x == TASK_INV) {
+                if (!wait_at_least(col_done + tk.y, discs[tk.y].n_col, false, A)) tk.x = -1;
+            }
+            s_task = tk;
+        }
+        __syncthreads();
+        const int4 tk = s_task;
+        if (tk.x < 0) break;
+        const BatchDisc<R> &D = discs[tk.y];
+        switch (tk.x) {
+        case TASK_FWD: task_fwd<R>(D, tk.z, tk.w, smem_raw); break;
+        case TASK_COL0:
+            if (D.nsrc == 1) task_col0<R, 1>(D, smem_raw);
+            else task_col0<R, 2>(D, smem_raw);
+            break;
+        case TASK_COL:
+            if (D.nsrc == 1) task_col<R, 1>(D, tk.w, smem_raw);
+            else task_col<R, 2>(D, tk.w, smem_raw);
+            break;
+        default: task_inv<R>(D, tk.z, tk.w, A, smem_raw); break;
+        }
+        if (tk.x != TASK_INV) {
+            __threadfence();                    // this thread's stores, before the count
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(tk.x == TASK_FWD ? fwd_done + tk.y : col_done + tk.y, 1u);
+        }
+    }
+}
+
+}  // namespace sg
+
+// ======================================================================
+// Host side
+// ======================================================================
+using namespace sg;
+
+struct sg_batch {
+    int n = 0;
+    bool f64 = false;
+    int device = 0, sms = 0, max_smem = 0;
+    std::vector<sg_plan *> plans;
+    std::vector<const void *> sg, sd;
+    std::vector<void *> outs;            // 6 per disc
+    uint32_t flags = 0;
+    unsigned long long timeout_ns = 0;
+    sg_batch_opts cfg{};                 // in use
+    int grid = 0, ntasks = 0;
+    float tuned_ms = 0.f;
+    void *discs = nullptr;               // BatchDisc<R>[n]
+    int4 *tasks = nullptr;
+    size_t tasks_cap = 0;
+    unsigned *ctl = nullptr, *flag = nullptr;
+    unsigned *gate_h = nullptr, *gate_d = nullptr;
+    cudaStream_t cs = nullptr;           // capture stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    char err[256] = {0};
+};
+
+namespace {
+
+sg_status bfail(sg_batch *b, sg_status s, const char *fmt, ...)
+{
+    if (b) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(b->err, sizeof(b->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+sg_status bcuda(sg_batch *b, cudaError_t e, const char *what)
+{
+    return bfail(b, e == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+uint32_t batch_outmask(const sg_batch *b, int k)
+{
+    uint32_t m = 0;
+    for (int q = 0; q < 6; ++q)
+        if (b->outs[6 * (size_t)k + q]) m |= 1u << q;
+    return m;
+}
+
+// Dynamic shared memory of one task of disc k with `threads` threads.
+size_t task_smem(const sg_plan *pl, int threads)
+{
+    const size_t esz = pl->f64 ? 16 : 8;
+    const int N = pl->p.nphi / 2, L = 2 * pl->p.nr;
+    const int Gr = threads / (N / 16), Gc = threads / (L / 16);
+    const size_t rows = 64 * sizeof(double) + (size_t)Gr * padded_len(N) * esz;
+    const size_t col = (size_t)Gc * (padded_len(L) + (pl->nsrc - 1) * 2 * L) * esz;
+    const size_t col0 = (size_t)Gc * (padded_len(L) + 2 * L) * esz;
+    return std::max(rows, std::max(col, col0));
+}
+
+struct TaskCounts {
+    unsigned fwd, col;
+};
+
+// Task list of one configuration; descriptors' wait targets filled in.
+template <typename R>
+void build_tasks(sg_batch *b, int threads, int order, std::vector<BatchDisc<R>> &dd, std::vector<int4> &tasks)
+{
+    const int n = b->n;
+    dd.assign(n, BatchDisc<R>{});
+    std::vector<std::vector<int4>> st[3];
+    for (auto &v : st) v.assign(n, {});
+    for (int k = 0; k < n; ++k) {
+        const sg_plan *pl = b->plans[k];
+        BatchDisc<R> &D = dd[k];
+        const int nr = pl->p.nr, nphi = pl->p.nphi, N = nphi / 2, L = 2 * nr;
+        D.s[0] = (const R *)b->sg[k];
+        D.s[1] = (const R *)b->sd[k];
+        D.sh = (cplx<R> *)pl->sh;
+        D.tab = (const cplx<R> *)pl->tab;
+        D.oh = (cplx<R> *)pl->oh;
+        for (int q = 0; q < 6; ++q) D.out[q] = (R *)b->outs[6 * (size_t)k + q];
+        D.rcen = (const R *)pl->rcen;
+        D.tw_row = (const cplx<R> *)pl->tw_row;
+        D.twp_row = (const cplx<R> *)pl->twp_row;
+        D.twp_col = (const cplx<R> *)pl->twp_col;
+        D.nr = nr;
+        D.nphi = nphi;
+        D.nsrc = pl->nsrc;
+        D.outmask = batch_outmask(b, k);
+        const int Gr = threads / (N / 16), Gc = threads / (L / 16);
+        const int rblocks = (nr + Gr - 1) / Gr;
+        const int cblocks = (N + Gc - 1) / Gc;       // tile 0 holds column 0's group (idle) and 1..Gc-1
+        for (int a = 0; a < pl->nsrc; ++a)
+            for (int r = 0; r < rblocks; ++r) st[0][k].push_back(make_int4(TASK_FWD, k, a, r));
+        st[1][k].push_back(make_int4(TASK_COL0, k, 0, 0));
+        for (int c = 0; c < cblocks; ++c)
+            if (c * Gc + Gc > 1) st[1][k].push_back(make_int4(TASK_COL, k, 0, c));
+        for (int q = 0; q < 6; ++q)
+            if ((D.outmask >> q) & 1u)
+                for (int r = 0; r < rblocks; ++r) st[2][k].push_back(make_int4(TASK_INV, k, q, r));
+        D.n_fwd = (unsigned)st[0][k].size();
+        D.n_col = (unsigned)st[1][k].size();
+    }
+    // largest discs first, so that small ones fill the tail
+    std::vector<int> ordk(n);
+    for (int k = 0; k < n; ++k) ordk[k] = k;
+    std::stable_sort(ordk.begin(), ordk.end(), [&](int x, int y) {
+        return (long)dd[x].nr * dd[x].nphi * dd[x].nsrc > (long)dd[y].nr * dd[y].nphi * dd[y].nsrc;
+    });
+    tasks.clear();
+    auto put = [&](int s, int k) { tasks.insert(tasks.end(), st[s][k].begin(), st[s][k].end()); };
+    if (order == SG_BATCH_ORDER_STAGED) {
+        for (int s = 0; s < 3; ++s)
+            for (int k : ordk) put(s, k);
+    } else {
+        for (int j = 0; j < n + 2; ++j) {
+            if (j < n) put(0, ordk[j]);
+            if (j >= 1 && j - 1 < n) put(1, ordk[j - 1]);
+            if (j >= 2) put(2, ordk[j - 2]);
+        }
+    }
+}
+
+template <typename R>
+sg_status configure(sg_batch *b, int threads, int ctas_per_sm, int order)
+{
+    std::vector<BatchDisc<R>> dd;
+    std::vector<int4> tasks;
+    build_tasks<R>(b, threads, order, dd, tasks);
+    size_t smem = 0;
+    for (int k = 0; k < b->n; ++k) smem = std::max(smem, task_smem(b->plans[k], threads));
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void *)k_batch<R>);
+    if (e != cudaSuccess) return bcuda(b, e, "kernel attributes");
+    const int dyn_max = b->max_smem - (int)fa.sharedSizeBytes;     // the kernel's static words come first
+    if (smem > (size_t)dyn_max) return bfail(b, SG_ERR_UNSUPPORTED, "batch needs %zu B of shared memory", smem);
+    // the device maximum, so that graphs of batches with other sizes stay launchable
+    e = cudaFuncSetAttribute((const void *)k_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    if (e != cudaSuccess) return bcuda(b, e, "shared-memory limit");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<R>, threads, smem);
+    if (e != cudaSuccess) return bcuda(b, e, "occupancy");
+    if (occ < 1) return bfail(b, SG_ERR_UNSUPPORTED, "batch kernel does not fit on an SM (%zu B)", smem);
+    const int cps = (ctas_per_sm <= 0 || ctas_per_sm > occ) ? occ : ctas_per_sm;
+    const int grid = std::min((int)tasks.size(), cps * b->sms);
+
+    if (tasks.size() > b->tasks_cap) {
+        if (b->tasks) cudaFree(b->tasks);
+        b->tasks = nullptr;
+        b->tasks_cap = 0;
+        e = cudaMalloc((void **)&b->tasks, tasks.size() * sizeof(int4));
+        if (e != cudaSuccess) return bcuda(b, e, "task list");
+        b->tasks_cap = tasks.size();
+    }
+    e = cudaMemcpy(b->tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->discs, dd.data(), dd.size() * sizeof(BatchDisc<R>), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bcuda(b, e, "task upload");
+
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    BatchArgs A{};
+    A.tasks = b->tasks;
+    A.ntasks = (int)tasks.size();
+    A.ndisc = b->n;
+    A.ctl = b->ctl;
+    A.flag = b->flag;
+    A.check_finite = (b->flags & SG_CHECK_FINITE) ? 1 : 0;
+    A.gate = (b->flags & SG_BATCH_HOST_GATE) ? b->gate_d : nullptr;
+    A.timeout_ns = b->timeout_ns;
+    e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "graph capture");
+    cudaMemsetAsync(b->ctl, 0, (2 + 2 * (size_t)b->n) * sizeof(unsigned), b->cs);
+    k_batch<R><<<grid, threads, smem, b->cs>>>((const BatchDisc<R> *)b->discs, A);
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(b->cs, &b->graph);
+    if (le != cudaSuccess) return bcuda(b, le, "batch launch");
+    if (e != cudaSuccess) return bcuda(b, e, "graph capture");
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
+    b->cfg.threads = threads;
+    b->cfg.ctas_per_sm = cps;
+    b->cfg.order = order;
+    b->grid = grid;
+    b->ntasks = (int)tasks.size();
+    return SG_OK;
+}
+
+sg_status configure_any(sg_batch *b, int threads, int cps, int order)
+{
+    return b->f64 ? configure<double>(b, threads, cps, order) : configure<float>(b, threads, cps, order);
+}
+
+bool threads_fit(const sg_batch *b, int threads)
+{
+    for (const sg_plan *pl : b->plans)
+        if (pl->p.nphi / 32 > threads || 2 * pl->p.nr / 16 > threads) return false;
+    return true;
+}
+
+// Time the current configuration: median of `reps` solves after 2 warm-ups.
+sg_status time_config(sg_batch *b, cudaStream_t s, int reps, float *ms)
+{
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<float> t;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < reps + 2 && e == cudaSuccess; ++r) {
+        cudaEventRecord(e0, s);
+        e = cudaGraphLaunch(b->exec, s);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float x = 0.f;
+        if (e == cudaSuccess && r >= 2) {
+            cudaEventElapsedTime(&x, e0, e1);
+            t.push_back(x);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return bcuda(b, e, "autotune run");
+    unsigned f = 0;
+    cudaMemcpy(&f, b->flag, sizeof(f), cudaMemcpyDeviceToHost);
+    if (f & 4u) return bfail(b, SG_ERR_TIMEOUT, "a device wait gave up while tuning");
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return SG_OK;
+}
+
+void batch_free(sg_batch *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    void *ptrs[] = {b->discs, b->tasks, b->ctl, b->flag};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    if (b->gate_h) cudaFreeHost(b->gate_h);
+    cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, const void *const *sigma_g,
+                          const void *const *sigma_d, void *const *outs, const sg_batch_opts *opts, void *stream)
+{
+    if (!out) return SG_ERR_ARG;
+    *out = nullptr;
+    if (!plans || n < 1 || !sigma_g || !outs) return SG_ERR_ARG;
+    sg_batch_opts o{};
+    if (opts) o = *opts;
+    auto reject = [&](sg_status s, const char *msg, int k) {
+        fprintf(stderr, "sg_batch_create: disc %d: %s\n", k, msg);
+        return s;
+    };
+    for (int k = 0; k < n; ++k) {
+        const sg_plan *pl = plans[k];
+        if (!pl) return reject(SG_ERR_ARG, "NULL plan", k);
+        if (pl->p.method != SG_METHOD_FFT) return reject(SG_ERR_ARG, "batches take FFT plans only", k);
+        if (pl->f64 != plans[0]->f64) return reject(SG_ERR_ARG, "mixed dtypes", k);
+        if (pl->device != plans[0]->device) return reject(SG_ERR_ARG, "plans on different devices", k);
+        if (!sigma_g[k]) return reject(SG_ERR_ARG, "sigma_g is NULL", k);
+        if (pl->nsrc == 2 && (!sigma_d || !sigma_d[k])) return reject(SG_ERR_ARG, "bi-fluid plan needs sigma_d", k);
+        if (pl->nsrc == 1)
+            for (int q = 3; q < 6; ++q)
+                if (outs[6 * (size_t)k + q]) return reject(SG_ERR_ARG, "dust output of a gas-only plan", k);
+    }
+    if (o.threads != 0 && o.threads != 256 && o.threads != 512) return reject(SG_ERR_ARG, "threads must be 256 or 512", -1);
+    if (o.order != SG_BATCH_ORDER_PIPELINED && o.order != SG_BATCH_ORDER_STAGED)
+        return reject(SG_ERR_ARG, "unknown order", -1);
+    if (!(o.timeout_ms >= 0) || o.timeout_ms > 600000) return reject(SG_ERR_ARG, "timeout_ms out of range", -1);
+
+    sg_batch *b = new (std::nothrow) sg_batch();
+    if (!b) return SG_ERR_OOM;
+    b->n = n;
+    b->f64 = plans[0]->f64;
+    b->device = plans[0]->device;
+    b->plans.assign(plans, plans + n);
+    b->sg.assign(sigma_g, sigma_g + n);
+    b->sd.assign(n, nullptr);
+    for (int k = 0; k < n; ++k)
+        if (plans[k]->nsrc == 2) b->sd[k] = sigma_d[k];
+    b->outs.assign(outs, outs + 6 * (size_t)n);
+    b->flags = o.flags;
+    b->timeout_ns = (unsigned long long)((o.timeout_ms > 0 ? o.timeout_ms : 2000.0) * 1e6);
+    auto bad = [&](sg_status st) {
+        fprintf(stderr, "sg_batch_create: %s\n", b->err);
+        batch_free(b);
+        delete b;
+        return st;
+    };
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->device);
+    if (e != cudaSuccess) return bad(bcuda(b, e, "device query"));
+    const size_t dsz = b->f64 ? sizeof(BatchDisc<double>) : sizeof(BatchDisc<float>);
+    e = cudaMalloc(&b->discs, dsz * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->ctl, (2 + 2 * (size_t)n) * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->flag, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->flag, 0, sizeof(unsigned));
+    if (e == cudaSuccess && (o.flags & SG_BATCH_HOST_GATE)) {
+        e = cudaHostAlloc((void **)&b->gate_h, sizeof(unsigned), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            *(volatile unsigned *)b->gate_h = 0u;
+            e = cudaHostGetDevicePointer((void **)&b->gate_d, b->gate_h, 0);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bad(bcuda(b, e, "batch allocation"));
+    // the plans' tables were built on their own streams; the batch reads them
+    e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return bad(bcuda(b, e, "stream sync"));
+
+    sg_status st;
+    if (o.autotune && !(o.flags & SG_BATCH_HOST_GATE)) {
+        float best = 0.f;
+        sg_batch_opts bc{};
+        bool have = false;
+        for (int threads : {256, 512}) {
+            if (!threads_fit(b, threads)) continue;
+            for (int order : {SG_BATCH_ORDER_PIPELINED, SG_BATCH_ORDER_STAGED}) {
+                for (int cps = 1; cps <= 8; ++cps) {
+                    st = configure_any(b, threads, cps, order);
+                    if (st == SG_ERR_UNSUPPORTED) break;
+                    if (st != SG_OK) return bad(st);
+                    if (b->cfg.ctas_per_sm < cps) break;     // past the occupancy maximum
+                    float ms = 0.f;
+                    st = time_config(b, (cudaStream_t)stream, 5, &ms);
+                    if (st != SG_OK) return bad(st);
+                    if (!have || ms < best) {
+                        best = ms;
+                        bc = b->cfg;
+                        have = true;
+                    }
+                }
+            }
+        }
+        if (!have) return bad(bfail(b, SG_ERR_UNSUPPORTED, "no batch configuration fits (transforms too long)"));
+        st = configure_any(b, bc.threads, bc.ctas_per_sm, bc.order);
+        if (st != SG_OK) return bad(st);
+        b->cfg.autotune = 1;
+        b->tuned_ms = best;
+    } else {
+        const int threads = o.threads ? o.threads : 256;
+        if (!threads_fit(b, threads))
+            return bad(bfail(b, SG_ERR_UNSUPPORTED, "a transform is longer than 16 x %d threads", threads));
+        st = configure_any(b, threads, o.ctas_per_sm, o.order);
+        if (st != SG_OK) return bad(st);
+    }
+    b->cfg.flags = b->flags;
+    b->cfg.timeout_ms = (double)b->timeout_ns * 1e-6;
+    e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemset(b->flag, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return bad(bcuda(b, e, "batch setup"));
+    *out = b;
+    return SG_OK;
+}
+
+sg_status sg_batch_solve(sg_batch *b, void *stream)
+{
+    if (!b) return SG_ERR_ARG;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bcuda(b, e, "set device");
+    if (b->gate_h) *(volatile unsigned *)b->gate_h = 0u;
+    e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return bcuda(b, e, "graph launch");
+    return SG_OK;
+}
+
+sg_status sg_batch_solve_loop(sg_batch *b, void *stream)
+{
+    if (!b) return SG_ERR_ARG;
+    for (int k = 0; k < b->n; ++k) {
+        void *const *o = b->outs.data() + 6 * (size_t)k;
+        sg_status st = sg_solve(b->plans[k], b->sg[k], b->sd[k], o[0], o[1], o[2], o[3], o[4], o[5], stream);
+        if (st != SG_OK) return bfail(b, st, "disc %d: %s", k, sg_last_error(b->plans[k]));
+    }
+    return SG_OK;
+}
+
+sg_status sg_batch_release(sg_batch *b)
+{
+    if (!b) return SG_ERR_ARG;
+    if (!b->gate_h) return bfail(b, SG_ERR_ARG, "batch was created without SG_BATCH_HOST_GATE");
+    __atomic_store_n(b->gate_h, 1u, __ATOMIC_SEQ_CST);
+    return SG_OK;
+}
+
+sg_status sg_batch_sync(sg_batch *b, void *stream)
+{
+    if (!b) return SG_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return bcuda(b, e, "stream sync");
+    unsigned f = 0;
+    e = cudaMemcpy(&f, b->flag, sizeof(f), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && f) e = cudaMemset(b->flag, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return bcuda(b, e, "flag read");
+    if (f & 4u) return bfail(b, SG_ERR_TIMEOUT, "a device-side wait gave up (outputs incomplete)");
+    if (f & 1u) return bfail(b, SG_ERR_NONFINITE, "non-finite output");
+    return SG_OK;
+}
+
+sg_status sg_batch_config(const sg_batch *b, sg_batch_opts *opts, int32_t *grid, int32_t *ntasks, float *tuned_ms)
+{
+    if (!b) return SG_ERR_ARG;
+    if (opts) *opts = b->cfg;
+    if (grid) *grid = b->grid;
+    if (ntasks) *ntasks = b->ntasks;
+    if (tuned_ms) *tuned_ms = b->tuned_ms;
+    return SG_OK;
+}
+
+void sg_batch_destroy(sg_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    batch_free(b);
+    delete b;
+}
+
+const char *sg_batch_last_error(const sg_batch *b) { return b ? b->err : ""; }
+
+}  // extern "C"

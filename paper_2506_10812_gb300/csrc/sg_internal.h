@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sg.h"
+
 namespace sg {
 
 // Twiddle tables: tw_row[k] = exp(-2 pi i k / nphi), k < nphi (the R2C /
@@ -20,7 +22,8 @@ int row_rpc(int nphi, bool f64);
 size_t row_smem_bytes(int nphi, int rpc, bool f64);
 size_t col_smem_bytes(int nr, int nsrc, bool f64);
 size_t tabcol_smem_bytes(int L, bool f64);
-__host__ __device__ int tab_pitch(int nr);   // complex slots per stored kernel-spectrum column (nr + 2)
+// complex slots per stored kernel-spectrum column
+__host__ __device__ inline int tab_pitch(int nr) { return nr + 2; }
 cudaError_t set_smem_limits(int max_optin);
 
 // Kernel-table evaluation (App. C lattice), one ordered pair (source aspect
@@ -84,3 +87,25 @@ cudaError_t launch_direct(int nr, int nphi, double r_in, double du, double G, co
                           unsigned int *flag, cudaStream_t s);
 
 }  // namespace sg
+
+// Plan state (sg_api.cu owns its lifetime; sg_batch_api.cu reads the buffers).
+struct sg_plan {
+    sg_params p{};
+    int nsrc = 1;
+    bool f64 = false;
+    int L = 0, N = 0;
+    double du = 0, dphi = 0;
+    int device = 0;
+    size_t esz = 4;                       // bytes per real element
+    void *tw_row = nullptr, *tw_row64 = nullptr;     // exp(-2 pi i k / nphi), k < nphi
+    void *twp_row = nullptr, *twp_row64 = nullptr;   // per-pass tables, length nphi / 2
+    void *twp_col = nullptr, *twp_col64 = nullptr;   // per-pass tables, length 2 nr
+    void *tab = nullptr, *sh = nullptr, *oh = nullptr;
+    void *rcen = nullptr, *geo_i = nullptr, *geo_j = nullptr;
+    void *Hg = nullptr, *Hd = nullptr;
+    unsigned int *flag = nullptr;         // bit 1: non-finite output, bit 2: staging timeout
+    double *ipart = nullptr;              // indirect-term partial sums
+    void *stage = nullptr;                // sg_solve_host: [2 inputs + 6 outputs][cells]
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events
+    char err[256] = {0};
+};

@@ -1,0 +1,98 @@
+// Shared device helpers of the FFT path: the column-blocked layout of the
+// [N][rows] spectral intermediates, the swizzled transpose tile of the row
+// transforms, and L2 cache-policy loads and stores.
+#pragma once
+
+#include <stdint.h>
+
+#include "sg_fft.cuh"
+
+namespace sg {
+
+constexpr int BW = 4;   // columns per block of the column-blocked layout
+
+// Swizzled [N][rpc] transpose tile: conflict-free for both the per-row
+// strided access (consecutive k, fixed row) and the blocked copy.
+template <typename C>
+__device__ __forceinline__ int tile_idx(int k, int g, int rpc)
+{
+    constexpr int lg_wf = sizeof(C) == 8 ? 4 : 3;         // log2(128 / sizeof(C))
+    const int lg_rpc = rpc == 4 ? 2 : (rpc == 2 ? 1 : 0);
+    return k * rpc + (g ^ ((k >> (lg_wf - lg_rpc)) & (rpc - 1)));
+}
+
+// The same swizzle for any power-of-two number of rows 2^lg (equal to
+// tile_idx for rpc = 1, 2, 4); for more than 16 rows (8-byte elements) the
+// XOR takes the low bits of k.
+template <typename C>
+__device__ __forceinline__ int tile_idx_g(int k, int g, int lg)
+{
+    constexpr int lg_wf = sizeof(C) == 8 ? 4 : 3;
+    const int sh = lg_wf > lg ? lg_wf - lg : 0;
+    return (k << lg) + (g ^ ((k >> sh) & ((1 << lg) - 1)));
+}
+
+// column-blocked index of element (m, i) in a [N][nrows] intermediate
+__device__ __forceinline__ size_t blk(int m, int i, int nrows)
+{
+    return ((size_t)(m >> 2) * nrows + i) * BW + (m & (BW - 1));
+}
+
+// ------------------------------------------------ L2 eviction policies
+// Per-instruction L2 cache hints (createpolicy): the kernel spectra stream
+// through L2 once per solve (evict-first); the column pass's output is read
+// again by the inverse row transforms right after (evict-last), so it should
+// stay in L2 instead of the streamed spectra.
+__device__ __forceinline__ uint64_t l2_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_hint(float2 *p, float2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_hint(double2 *p, double2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float2 ld_hint(const float2 *p, uint64_t pol)
+{
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_hint(const double2 *p, uint64_t pol)
+{
+    double2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Coherent load (L2 only, no L1 allocation, no non-coherent path) for data
+// that other blocks of the same launch wrote.
+__device__ __forceinline__ float2 ld_cg_hint(const float2 *p, uint64_t pol)
+{
+    float2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ double2 ld_cg_hint(const double2 *p, uint64_t pol)
+{
+    double2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol)
+                 : "memory");
+    return v;
+}
+
+}  // namespace sg

@@ -24,6 +24,10 @@ Recipes (all numpy PCG64, seed = 2506108120 + recipe offset):
                      correlation length 5 cells (white noise filtered in
                      Fourier space on a [2 nr, nphi] grid, periodic in phi,
                      cropped to nr rows), psi_m uniform phases.
+``batch_discs``      n independent gas + dust discs (default 64): grid drawn from
+                     {128x256, 256x512, 512x1024, 1024x2048}, h_g uniform in [0.03, 0.1],
+                     St from {0.01, 0.1, 1}, each a log-normal disc (recipe above,
+                     its own seed) with a 1 % dust fraction.
 ``clumpy_gas``       Gaussian clumps Sigma (1 + A exp(-|r - r_c|^2 / 2 R^2)) on a
                      smooth r^-1 disc, the clump form of the paper's Gaussian
                      discs test (Sec. 4.4).
@@ -153,3 +157,20 @@ def ragged_noise(nr, nphi, r_in=0.3, r_out=3.0, h=0.07, G=1.0, offset=5, bifluid
     sd = 0.01 * rng.uniform(0.5, 1.5, (nr, nphi)) if bifluid else None
     return Disc(nr, nphi, r_in, r_out, h, float(dust_aspect_ratio(h, St)) if bifluid else None,
                 G, sg, sd, f"noise {nr}x{nphi}")
+
+
+BATCH_SHAPES = ((128, 256), (256, 512), (512, 1024), (1024, 2048))
+
+
+def batch_discs(n=64, offset=10, shapes=BATCH_SHAPES, St_choices=(0.01, 0.1, 1.0)):
+    """n independent gas + dust discs of uneven size (see the module docstring)."""
+    rng = _rng(offset)
+    discs = []
+    for k in range(n):
+        nr, nphi = shapes[int(rng.integers(len(shapes)))]
+        h = float(rng.uniform(0.03, 0.1))
+        St = float(St_choices[int(rng.integers(len(St_choices)))])
+        d = lognormal_bifluid(nr, nphi, St=St, offset=offset + 1 + k, h=h)
+        discs.append(d)
+    return discs
+

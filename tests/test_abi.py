@@ -86,6 +86,18 @@ def test_null_arguments(lib):
     assert lib.sg_launches_per_solve(None, 7) == 0
     lib.sg_destroy(None)
     assert lib.sg_last_error(None) == b""
+    # batch entry points reject NULL / empty batches before any CUDA call
+    assert lib.sg_batch_create(None, None, 0, None, None, None, None, None) == N.SG_ERR_ARG
+    assert lib.sg_batch_create(ctypes.byref(h), None, 1, None, None, None, None, None) == N.SG_ERR_ARG
+    assert h.value is None
+    plans = (ctypes.c_void_p * 1)(None)
+    assert lib.sg_batch_create(ctypes.byref(h), plans, 0, plans, plans, plans, None, None) == N.SG_ERR_ARG
+    for fn in (lib.sg_batch_solve, lib.sg_batch_solve_loop, lib.sg_batch_sync):
+        assert fn(None, None) == N.SG_ERR_ARG
+    assert lib.sg_batch_release(None) == N.SG_ERR_ARG
+    assert lib.sg_batch_config(None, None, None, None, None) == N.SG_ERR_ARG
+    lib.sg_batch_destroy(None)
+    assert lib.sg_batch_last_error(None) == b""
 
 
 def test_status_strings(lib):
