@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batch", action="store_true",
                     help="64 uneven gas + dust discs per step instead of one 2048 x 4096 disc")
+    ap.add_argument("--batch-n", type=int, default=64, help="discs in the batch (the first n of the 64)")
+    ap.add_argument("--batch-config", default="auto",
+                    help="'auto' (autotune) or threads,ctas_per_sm,order (e.g. 256,2,staged)")
+    ap.add_argument("--no-loop", action="store_true", help="batch mode: skip timing the per-disc loops")
     return ap.parse_args()
 
 
@@ -388,7 +392,7 @@ def run_batch(args):
     import torch
     from paper_2506_10812_gb300 import Batch, Plan, inputs
     dev = torch.device("cuda", torch.cuda.current_device())
-    discs = inputs.batch_discs()
+    discs = inputs.batch_discs()[:args.batch_n]
     t0 = time.perf_counter()
     plans = [Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, device=dev) for d in discs]
     build_ms = (time.perf_counter() - t0) * 1e3
@@ -396,9 +400,14 @@ def run_batch(args):
     sd = [torch.tensor(d.sigma_d, dtype=torch.float32, device=dev) for d in discs]
     outs = [p.solve(g, x) for p, g, x in zip(plans, sg, sd)]
     t0 = time.perf_counter()
-    batch = Batch(plans, sg, sd, outs, autotune=True)
+    if args.batch_config == "auto":
+        batch = Batch(plans, sg, sd, outs, autotune=True)
+    else:
+        th, cps, order = args.batch_config.split(",")
+        batch = Batch(plans, sg, sd, outs, threads=int(th), ctas_per_sm=int(cps), order=order)
     tune_ms = (time.perf_counter() - t0) * 1e3
     cfg = batch.config()
+    tried = batch.tune_results()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def py_loop():
@@ -428,8 +437,11 @@ def run_batch(args):
     K, W = args.steps, args.warmup
     ms_graph, clk = timed(batch.solve, K, W, ClockSampler(dev.index))
     batch.sync()
-    ms_loop_c, _ = timed(batch.solve_loop, min(K, 50), W)
-    ms_loop_py, _ = timed(py_loop, min(K, 20), W)
+    if args.no_loop:
+        ms_loop_c = ms_loop_py = float("nan")
+    else:
+        ms_loop_c, _ = timed(batch.solve_loop, min(K, 50), W)
+        ms_loop_py, _ = timed(py_loop, min(K, 20), W)
     batch.sync()
     cells = sum(d.cells for d in discs)
     model = sum(step_model_bytes(d.nr, d.nphi, 2, 6) for d in discs)
@@ -440,13 +452,14 @@ def run_batch(args):
     result = {"metric": METRIC, "value": cells / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
               "warmup": W, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic (64 seeded log-normal gas + dust discs)",
-              "config": {"workload": "64 independent gas + dust discs, grids drawn from 128x256..1024x2048, "
+              "config": {"workload": f"{len(discs)} independent gas + dust discs, grids drawn from 128x256..1024x2048, "
                                      "h_g in [0.03, 0.1], St in {0.01, 0.1, 1}, outputs Phi + g_r + g_phi "
                                      "per fluid; one persistent launch per step from a CUDA graph",
                          "shapes": dict(shapes), "cells": cells,
                          "l2": "flushed between timed steps (256 MiB write)",
                          "kernel_spectra": "built once per plan, outside the timed steps"},
               "batch_config": cfg,
+              "autotune_candidates": [dict(c, ms=round(m, 4)) for c, m in tried],
               "roofline": {"bound": "hbm", "kernel": "k_batch (persistent, whole step)",
                            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(achieved / peak, 4), "traffic": None,

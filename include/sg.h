@@ -240,9 +240,13 @@ typedef struct {
                               stages of consecutive discs (disc k's rows, k-1's
                               columns, k-2's inverse rows); _STAGED runs every
                               disc's stage s before any stage s+1               */
-    int32_t autotune;      /* 1: time every (threads, ctas_per_sm, order)
-                              candidate on the bound buffers at create and keep
-                              the fastest; threads/ctas_per_sm/order are ignored   */
+    int32_t specialize;    /* 1: FP32 transforms of the lengths sg_solve compiles
+                              for (rows of nphi 2048 and 4096, columns of 2 nr =
+                              1024, 2048, 4096) use compile-time kernels; other
+                              lengths and FP64 stay generic                      */
+    int32_t autotune;      /* 1: time every (specialize, threads, ctas_per_sm,
+                              order) candidate on the bound buffers at create and
+                              keep the fastest; those four fields are ignored   */
     uint32_t flags;        /* SG_CHECK_FINITE, SG_BATCH_HOST_GATE                   */
     double timeout_ms;     /* bound of each device-side wait (0: 2000 ms)          */
 } sg_batch_opts;
@@ -292,6 +296,12 @@ sg_status sg_batch_sync(sg_batch *batch, void *stream);
  * time per solve in ms (0 when not tuned); any pointer may be NULL.       */
 sg_status sg_batch_config(const sg_batch *batch, sg_batch_opts *opts, int32_t *grid,
                           int32_t *ntasks, float *tuned_ms);
+
+/* The autotuner's candidates in the order they were timed: writes up to
+ * `max` configurations to cfgs and their median times per solve (ms) to ms
+ * (either may be NULL) and returns how many were timed (0 without
+ * autotune; -1 for a NULL batch).                                         */
+int32_t sg_batch_tune_results(const sg_batch *batch, int32_t max, sg_batch_opts *cfgs, float *ms);
 
 /* Release the batch (not its plans or buffers).  Synchronises the device. */
 void sg_batch_destroy(sg_batch *batch);

@@ -24,7 +24,7 @@ SG_BATCH_ORDER_PIPELINED, SG_BATCH_ORDER_STAGED = 0, 1
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
            "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_batch_create", "sg_batch_solve",
-           "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_destroy",
+           "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_tune_results", "sg_batch_destroy",
            "sg_batch_last_error", "sg_destroy", "sg_status_string", "sg_last_error")
 
 
@@ -39,7 +39,7 @@ class SgParams(ctypes.Structure):
 
 class SgBatchOpts(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("flags", ctypes.c_uint32), ("timeout_ms", ctypes.c_double)]
+                ("specialize", ctypes.c_int32), ("autotune", ctypes.c_int32), ("flags", ctypes.c_uint32), ("timeout_ms", ctypes.c_double)]
 
 
 class SgError(RuntimeError):
@@ -95,6 +95,8 @@ def load() -> ctypes.CDLL:
     lib.sg_batch_config.argtypes = [vp, ctypes.POINTER(SgBatchOpts), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                     ctypes.POINTER(ctypes.c_float)]
     lib.sg_batch_config.restype = st
+    lib.sg_batch_tune_results.argtypes = [vp, i32, ctypes.POINTER(SgBatchOpts), ctypes.POINTER(ctypes.c_float)]
+    lib.sg_batch_tune_results.restype = i32
     lib.sg_batch_destroy.argtypes = [vp]
     lib.sg_batch_destroy.restype = None
     lib.sg_batch_last_error.argtypes = [vp]

@@ -17,12 +17,13 @@ class Batch:
     ``sigma_g[k]``, ``sigma_d[k]`` (None for a gas-only plan) and ``outs[k]``
     (dict keyed like ``Plan.solve``'s result; missing keys are not computed)
     must stay alive and at the same addresses for the batch's lifetime.
-    ``threads`` (256 / 512), ``ctas_per_sm`` and ``order`` ("pipelined" /
-    "staged") fix the launch shape unless ``autotune`` times every candidate
-    and keeps the fastest."""
+    ``threads`` (256 / 512), ``ctas_per_sm``, ``order`` ("pipelined" /
+    "staged") and ``specialize`` (compile-time transforms for the lengths the
+    per-disc path specialises) fix the launch unless ``autotune`` times every
+    candidate and keeps the fastest."""
 
     def __init__(self, plans, sigma_g, sigma_d, outs, threads=0, ctas_per_sm=0, order="pipelined",
-                 autotune=False, check_finite=False, host_gate=False, timeout_ms=0.0):
+                 specialize=False, autotune=False, check_finite=False, host_gate=False, timeout_ms=0.0):
         self._lib = N.load()
         n = len(plans)
         if not (len(sigma_g) == len(sigma_d) == len(outs) == n) or n < 1:
@@ -47,6 +48,7 @@ class Batch:
         o = N.SgBatchOpts()
         o.threads, o.ctas_per_sm = int(threads), int(ctas_per_sm)
         o.order = {"pipelined": N.SG_BATCH_ORDER_PIPELINED, "staged": N.SG_BATCH_ORDER_STAGED}[order]
+        o.specialize = 1 if specialize else 0
         o.autotune = 1 if autotune else 0
         o.flags = (N.SG_CHECK_FINITE if check_finite else 0) | (N.SG_BATCH_HOST_GATE if host_gate else 0)
         o.timeout_ms = float(timeout_ms)
@@ -84,8 +86,18 @@ class Batch:
         N.check(self._lib.sg_batch_config(self._h, ctypes.byref(o), ctypes.byref(grid), ctypes.byref(ntasks),
                                           ctypes.byref(ms)), what="sg_batch_config", batch_handle=self._h)
         return {"threads": o.threads, "ctas_per_sm": o.ctas_per_sm,
-                "order": ("pipelined", "staged")[o.order], "autotuned": bool(o.autotune),
+                "order": ("pipelined", "staged")[o.order], "specialize": bool(o.specialize),
+                "autotuned": bool(o.autotune),
                 "grid": grid.value, "tasks": ntasks.value, "tuned_ms": ms.value, "timeout_ms": o.timeout_ms}
+
+    def tune_results(self):
+        """[(config dict, ms per solve)] of every autotune candidate."""
+        n = self._lib.sg_batch_tune_results(self._h, 0, None, None)
+        cfgs = (N.SgBatchOpts * max(n, 1))()
+        ms = (ctypes.c_float * max(n, 1))()
+        self._lib.sg_batch_tune_results(self._h, n, cfgs, ms)
+        return [({"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "order": ("pipelined", "staged")[c.order],
+                  "specialize": bool(c.specialize)}, float(m)) for c, m in zip(cfgs[:n], ms[:n])]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -112,7 +112,7 @@ __device__ bool wait_at_least(const unsigned *p, unsigned target, bool sys, cons
 // ------------------------------------------------------------ row R2C task
 // Rows rb G .. rb G + G - 1 of source `a` (rows past nr recompute row nr - 1
 // and store nothing).  Same arithmetic as k_rows_fwd.
-template <typename R>
+template <typename R, int NC>
 __device__ void task_fwd(const BatchDisc<R> &D, int a, int rb, unsigned char *smem)
 {
     using C = cplx<R>;
@@ -146,7 +146,7 @@ __device__ void task_fwd(const BatchDisc<R> &D, int a, int rb, unsigned char *sm
     const R mean = s / (R)nphi;
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = mkc<C>(v[e].x - mean, v[e].y - mean);
-    fft_reg<true>(v, N, T, t, xb, D.twp_row);
+    fft_any<true, NC>(v, N, T, t, xb, D.twp_row);
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 16; ++e) xb[pidx(t + T * e)] = v[e];
@@ -188,7 +188,7 @@ __device__ __forceinline__ C tab_at(const C *col, int k, int H, bool upper, uint
 
 // Columns cb G + g (1 <= m < N; other groups recompute column N - 1 or 1 and
 // store nothing).  Same arithmetic as k_cols.
-template <typename R, int NS>
+template <typename R, int NS, int LC>
 __device__ void task_col(const BatchDisc<R> &D, int cb, unsigned char *smem)
 {
     using C = cplx<R>;
@@ -210,7 +210,7 @@ __device__ void task_col(const BatchDisc<R> &D, int cb, unsigned char *smem)
         for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(src + blk(mv, t + T * e, nr), pf);
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
-        fft_reg<true>(v, L, T, t, xb, D.twp_col);
+        fft_any<true, LC>(v, L, T, t, xb, D.twp_col);
         if constexpr (NS == 1) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) spec[e] = v[e];
@@ -242,7 +242,7 @@ __device__ void task_col(const BatchDisc<R> &D, int cb, unsigned char *smem)
             }
             v[e] = acc;
         }
-        fft_reg<false>(v, L, T, t, xb, D.twp_col);
+        fft_any<false, LC>(v, L, T, t, xb, D.twp_col);
         if (valid) {
             C *o = D.oh + (size_t)q * N * nr;
 #pragma unroll
@@ -306,7 +306,7 @@ __device__ void task_col0(const BatchDisc<R> &D, unsigned char *smem)
 
 // ------------------------------------------------- row C2R + epilogue task
 // Rows rb G .. of output slot q.  Same arithmetic as k_rows_inv.
-template <typename R>
+template <typename R, int NC>
 __device__ void task_inv(const BatchDisc<R> &D, int q, int rb, const BatchArgs &A, unsigned char *smem)
 {
     using C = cplx<R>;
@@ -350,7 +350,7 @@ __device__ void task_inv(const BatchDisc<R> &D, int q, int rb, const BatchArgs &
             v[e] = cadd(cadd(X, Xc), cmul_i(cmulc(csub(X, Xc), __ldg(&D.tw_row[k]))));
         }
     }
-    fft_reg<false>(v, N, T, t, sm + g * padded_len(N), D.twp_row);
+    fft_any<false, NC>(v, N, T, t, sm + g * padded_len(N), D.twp_row);
     const int i = i0 + g;
     if (i < nr) {
         const R sc = (q % 3) == 0 ? (R)1 : (R)1 / D.rcen[i];
@@ -366,26 +366,81 @@ __device__ void task_inv(const BatchDisc<R> &D, int q, int rb, const BatchArgs &
     }
 }
 
-// ------------------------------------------------------- persistent kernel
+// ------------------------------------------------------------ L2 prefetch
+// One bulk prefetch into L2 (address and size multiples of 16 bytes).
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The read-only data a task reads first: the input rows of a row task; the
+// kernel-spectrum columns and the column blocks of the row spectra of a
+// column task.  Every range lies inside its buffer; (nr + 2) complex per
+// spectrum column, nphi reals per row and nr x 4 complex per column block
+// are multiples of 16 bytes.
 template <typename R>
+__device__ void prefetch_task(const BatchDisc<R> &D, int4 tk, int threads)
+{
+    using C = cplx<R>;
+    const int nr = D.nr, nphi = D.nphi, N = nphi >> 1, L = 2 * nr, P = tab_pitch(nr), ns = D.nsrc;
+    if (tk.x == TASK_FWD) {
+        const int G = threads / (N >> 4);
+        const int i0 = tk.w * G, rows = min(G, nr - i0);
+        prefetch_l2(D.s[tk.z] + (size_t)i0 * nphi, (unsigned)((size_t)rows * nphi * sizeof(R)));
+    } else if (tk.x == TASK_COL || tk.x == TASK_COL0) {
+        const int G = threads / (L >> 4);
+        const int m0 = tk.x == TASK_COL ? tk.w * G : 0;
+        const int cols = tk.x == TASK_COL ? min(G, N - m0) : 1;
+        for (int q = 0; q < 3 * ns; ++q) {
+            if (!((D.outmask >> q) & 1u)) continue;
+            const int b = q / 3, c = q - 3 * b;
+            for (int a = 0; a < ns; ++a) {
+                const C *t0 = D.tab + (size_t)((a * ns + b) * 3 + c) * (N + 1) * P;
+                prefetch_l2(t0 + (size_t)m0 * P, (unsigned)((size_t)cols * P * sizeof(C)));
+                if (tk.x == TASK_COL0) prefetch_l2(t0 + (size_t)N * P, (unsigned)(P * sizeof(C)));
+            }
+        }
+        const int b0 = m0 >> 2, b1 = (m0 + cols - 1) >> 2;
+        for (int a = 0; a < ns; ++a)
+            prefetch_l2(D.sh + (size_t)a * N * nr + (size_t)b0 * nr * BW,
+                        (unsigned)((size_t)(b1 - b0 + 1) * nr * BW * sizeof(C)));
+    }
+}
+
+// ------------------------------------------------------- persistent kernel
+// SPEC: the row transforms of nphi = 2048, 4096 and the column transforms of
+// length 1024, 2048, 4096 use the compile-time variant of sg_fft.cuh (FP32).
+template <typename R, bool SPEC>
 __global__ void __launch_bounds__(512) k_batch(const BatchDisc<R> *__restrict__ discs, const __grid_constant__ BatchArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int4 s_task;
+    __shared__ int4 s_task, s_ahead;          // s_ahead: thread 0 only
     unsigned *next = A.ctl, *fwd_done = A.ctl + 2, *col_done = A.ctl + 2 + A.ndisc;
     if (A.gate) {
         if (threadIdx.x == 0) s_task.x = wait_at_least(A.gate, 1u, true, A) ? 0 : -1;
         __syncthreads();
         if (s_task.x < 0) return;
     }
+    // Thread 0 holds the next task while the block runs the current one and
+    // prefetches its read-only data into L2.  A held task only waits on tasks
+    // earlier in the list, and its holder finishes its current (earlier) task
+    // first, so holding one task ahead keeps the waits acyclic.
+    auto dequeue = [&]() {
+        int4 tk = make_int4(-1, 0, 0, 0);
+        if (!ld_acquire_gpu(A.ctl + 1)) {
+            const unsigned i = atomicAdd(next, 1u);
+            if (i < (unsigned)A.ntasks) tk = A.tasks[i];
+        }
+        return tk;
+    };
+    if (threadIdx.x == 0) s_ahead = dequeue();
     for (;;) {
         __syncthreads();                        // every thread has read the previous s_task
         if (threadIdx.x == 0) {
-            int4 tk = make_int4(-1, 0, 0, 0);
-            if (!ld_acquire_gpu(A.ctl + 1)) {
-                const unsigned i = atomicAdd(next, 1u);
-                if (i < (unsigned)A.ntasks) tk = A.tasks[i];
-            }
+            int4 tk = s_ahead;
+            const int4 ahead = tk.x >= 0 ? dequeue() : make_int4(-1, 0, 0, 0);
+            s_ahead = ahead;
+            if (ahead.x >= 0) prefetch_task<R>(discs[ahead.y], ahead, blockDim.x);
             if (tk.x == TASK_COL0 || tk.x == TASK_COL) {
                 if (!wait_at_least(fwd_done + tk.y, discs[tk.y].n_fwd, false, A)) tk.x = -1;
             } else if (tk.x == TASK_INV) {
@@ -398,16 +453,33 @@ __global__ void __launch_bounds__(512) k_batch(const BatchDisc<R> *__restrict__ 
         if (tk.x < 0) break;
         const BatchDisc<R> &D = discs[tk.y];
         switch (tk.x) {
-        case TASK_FWD: task_fwd<R>(D, tk.z, tk.w, smem_raw); break;
+        case TASK_FWD:
+            if (SPEC && D.nphi == 4096) task_fwd<R, SPEC ? 2048 : 0>(D, tk.z, tk.w, smem_raw);
+            else if (SPEC && D.nphi == 2048) task_fwd<R, SPEC ? 1024 : 0>(D, tk.z, tk.w, smem_raw);
+            else task_fwd<R, 0>(D, tk.z, tk.w, smem_raw);
+            break;
         case TASK_COL0:
             if (D.nsrc == 1) task_col0<R, 1>(D, smem_raw);
             else task_col0<R, 2>(D, smem_raw);
             break;
         case TASK_COL:
-            if (D.nsrc == 1) task_col<R, 1>(D, tk.w, smem_raw);
-            else task_col<R, 2>(D, tk.w, smem_raw);
+            if (D.nsrc == 1) {
+                if (SPEC && D.nr == 2048) task_col<R, 1, SPEC ? 4096 : 0>(D, tk.w, smem_raw);
+                else if (SPEC && D.nr == 1024) task_col<R, 1, SPEC ? 2048 : 0>(D, tk.w, smem_raw);
+                else if (SPEC && D.nr == 512) task_col<R, 1, SPEC ? 1024 : 0>(D, tk.w, smem_raw);
+                else task_col<R, 1, 0>(D, tk.w, smem_raw);
+            } else {
+                if (SPEC && D.nr == 2048) task_col<R, 2, SPEC ? 4096 : 0>(D, tk.w, smem_raw);
+                else if (SPEC && D.nr == 1024) task_col<R, 2, SPEC ? 2048 : 0>(D, tk.w, smem_raw);
+                else if (SPEC && D.nr == 512) task_col<R, 2, SPEC ? 1024 : 0>(D, tk.w, smem_raw);
+                else task_col<R, 2, 0>(D, tk.w, smem_raw);
+            }
             break;
-        default: task_inv<R>(D, tk.z, tk.w, A, smem_raw); break;
+        default:
+            if (SPEC && D.nphi == 4096) task_inv<R, SPEC ? 2048 : 0>(D, tk.z, tk.w, A, smem_raw);
+            else if (SPEC && D.nphi == 2048) task_inv<R, SPEC ? 1024 : 0>(D, tk.z, tk.w, A, smem_raw);
+            else task_inv<R, 0>(D, tk.z, tk.w, A, smem_raw);
+            break;
         }
         if (tk.x != TASK_INV) {
             __threadfence();                    // this thread's stores, before the count
@@ -436,6 +508,8 @@ struct sg_batch {
     sg_batch_opts cfg{};                 // in use
     int grid = 0, ntasks = 0;
     float tuned_ms = 0.f;
+    std::vector<sg_batch_opts> tried;    // autotune candidates and their times
+    std::vector<float> tried_ms;
     void *discs = nullptr;               // BatchDisc<R>[n]
     int4 *tasks = nullptr;
     size_t tasks_cap = 0;
@@ -550,8 +624,20 @@ void build_tasks(sg_batch *b, int threads, int order, std::vector<BatchDisc<R>> 
     }
 }
 
+template <typename R, bool SPEC>
+sg_status configure_k(sg_batch *b, int threads, int ctas_per_sm, int order);
+
 template <typename R>
-sg_status configure(sg_batch *b, int threads, int ctas_per_sm, int order)
+sg_status configure(sg_batch *b, int threads, int ctas_per_sm, int order, bool spec)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (spec) return configure_k<R, true>(b, threads, ctas_per_sm, order);
+    }
+    return configure_k<R, false>(b, threads, ctas_per_sm, order);
+}
+
+template <typename R, bool SPEC>
+sg_status configure_k(sg_batch *b, int threads, int ctas_per_sm, int order)
 {
     std::vector<BatchDisc<R>> dd;
     std::vector<int4> tasks;
@@ -559,15 +645,15 @@ sg_status configure(sg_batch *b, int threads, int ctas_per_sm, int order)
     size_t smem = 0;
     for (int k = 0; k < b->n; ++k) smem = std::max(smem, task_smem(b->plans[k], threads));
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, (const void *)k_batch<R>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, (const void *)k_batch<R, SPEC>);
     if (e != cudaSuccess) return bcuda(b, e, "kernel attributes");
     const int dyn_max = b->max_smem - (int)fa.sharedSizeBytes;     // the kernel's static words come first
     if (smem > (size_t)dyn_max) return bfail(b, SG_ERR_UNSUPPORTED, "batch needs %zu B of shared memory", smem);
     // the device maximum, so that graphs of batches with other sizes stay launchable
-    e = cudaFuncSetAttribute((const void *)k_batch<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    e = cudaFuncSetAttribute((const void *)k_batch<R, SPEC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return bcuda(b, e, "shared-memory limit");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<R>, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<R, SPEC>, threads, smem);
     if (e != cudaSuccess) return bcuda(b, e, "occupancy");
     if (occ < 1) return bfail(b, SG_ERR_UNSUPPORTED, "batch kernel does not fit on an SM (%zu B)", smem);
     const int cps = (ctas_per_sm <= 0 || ctas_per_sm > occ) ? occ : ctas_per_sm;
@@ -601,7 +687,7 @@ sg_status configure(sg_batch *b, int threads, int ctas_per_sm, int order)
     e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "graph capture");
     cudaMemsetAsync(b->ctl, 0, (2 + 2 * (size_t)b->n) * sizeof(unsigned), b->cs);
-    k_batch<R><<<grid, threads, smem, b->cs>>>((const BatchDisc<R> *)b->discs, A);
+    k_batch<R, SPEC><<<grid, threads, smem, b->cs>>>((const BatchDisc<R> *)b->discs, A);
     cudaError_t le = cudaGetLastError();
     e = cudaStreamEndCapture(b->cs, &b->graph);
     if (le != cudaSuccess) return bcuda(b, le, "batch launch");
@@ -611,14 +697,15 @@ sg_status configure(sg_batch *b, int threads, int ctas_per_sm, int order)
     b->cfg.threads = threads;
     b->cfg.ctas_per_sm = cps;
     b->cfg.order = order;
+    b->cfg.specialize = SPEC ? 1 : 0;
     b->grid = grid;
     b->ntasks = (int)tasks.size();
     return SG_OK;
 }
 
-sg_status configure_any(sg_batch *b, int threads, int cps, int order)
+sg_status configure_any(sg_batch *b, int threads, int cps, int order, bool spec)
 {
-    return b->f64 ? configure<double>(b, threads, cps, order) : configure<float>(b, threads, cps, order);
+    return b->f64 ? configure<double>(b, threads, cps, order, false) : configure<float>(b, threads, cps, order, spec);
 }
 
 bool threads_fit(const sg_batch *b, int threads)
@@ -749,17 +836,20 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, cons
         float best = 0.f;
         sg_batch_opts bc{};
         bool have = false;
+        for (int spec = 0; spec <= (b->f64 ? 0 : 1); ++spec)
         for (int threads : {256, 512}) {
             if (!threads_fit(b, threads)) continue;
             for (int order : {SG_BATCH_ORDER_PIPELINED, SG_BATCH_ORDER_STAGED}) {
                 for (int cps = 1; cps <= 8; ++cps) {
-                    st = configure_any(b, threads, cps, order);
+                    st = configure_any(b, threads, cps, order, spec != 0);
                     if (st == SG_ERR_UNSUPPORTED) break;
                     if (st != SG_OK) return bad(st);
                     if (b->cfg.ctas_per_sm < cps) break;     // past the occupancy maximum
                     float ms = 0.f;
                     st = time_config(b, (cudaStream_t)stream, 5, &ms);
                     if (st != SG_OK) return bad(st);
+                    b->tried.push_back(b->cfg);
+                    b->tried_ms.push_back(ms);
                     if (!have || ms < best) {
                         best = ms;
                         bc = b->cfg;
@@ -769,7 +859,7 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, cons
             }
         }
         if (!have) return bad(bfail(b, SG_ERR_UNSUPPORTED, "no batch configuration fits (transforms too long)"));
-        st = configure_any(b, bc.threads, bc.ctas_per_sm, bc.order);
+        st = configure_any(b, bc.threads, bc.ctas_per_sm, bc.order, bc.specialize != 0);
         if (st != SG_OK) return bad(st);
         b->cfg.autotune = 1;
         b->tuned_ms = best;
@@ -777,7 +867,7 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, cons
         const int threads = o.threads ? o.threads : 256;
         if (!threads_fit(b, threads))
             return bad(bfail(b, SG_ERR_UNSUPPORTED, "a transform is longer than 16 x %d threads", threads));
-        st = configure_any(b, threads, o.ctas_per_sm, o.order);
+        st = configure_any(b, threads, o.ctas_per_sm, o.order, o.specialize != 0);
         if (st != SG_OK) return bad(st);
     }
     b->cfg.flags = b->flags;
@@ -841,6 +931,17 @@ sg_status sg_batch_config(const sg_batch *b, sg_batch_opts *opts, int32_t *grid,
     if (ntasks) *ntasks = b->ntasks;
     if (tuned_ms) *tuned_ms = b->tuned_ms;
     return SG_OK;
+}
+
+int32_t sg_batch_tune_results(const sg_batch *b, int32_t max, sg_batch_opts *cfgs, float *ms)
+{
+    if (!b) return -1;
+    const int n = (int)b->tried.size();
+    for (int i = 0; i < n && i < max; ++i) {
+        if (cfgs) cfgs[i] = b->tried[i];
+        if (ms) ms[i] = b->tried_ms[i];
+    }
+    return n;
 }
 
 void sg_batch_destroy(sg_batch *b)

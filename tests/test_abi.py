@@ -96,6 +96,7 @@ def test_null_arguments(lib):
         assert fn(None, None) == N.SG_ERR_ARG
     assert lib.sg_batch_release(None) == N.SG_ERR_ARG
     assert lib.sg_batch_config(None, None, None, None, None) == N.SG_ERR_ARG
+    assert lib.sg_batch_tune_results(None, 0, None, None) == -1
     lib.sg_batch_destroy(None)
     assert lib.sg_batch_last_error(None) == b""
 

@@ -151,6 +151,43 @@ def test_launch_configurations_are_bit_identical():
         S.close()
 
 
+def test_specialized_transforms():
+    """The length-specialised kernel: bit-identical to sg_solve where both use
+    the compile-time transforms (1024 x 2048: rows of 2048, columns of 2048),
+    within FP32 rounding of the generic batch elsewhere, and independent of
+    the launch configuration."""
+    discs = [rounded(inputs.lognormal_bifluid(1024, 2048, St=0.1, offset=170)),
+             rounded(inputs.lognormal_bifluid(512, 1024, St=1.0, offset=171)),
+             rounded(inputs.lognormal_gas(256, 4096, offset=172))]
+    S = Setup(discs)
+    try:
+        ref = S.per_disc()
+        with S.batch() as b:
+            b.solve()
+            b.sync()
+            generic = [{x: o[x].clone() for x in o} for o in S.out]
+        first = None
+        for threads, order in ((256, "staged"), (512, "pipelined")):
+            with S.batch(specialize=True, threads=threads, order=order) as b:
+                assert b.config()["specialize"]
+                b.solve()
+                b.sync()
+                cur = [{x: o[x].clone() for x in o} for o in S.out]
+            if first is None:
+                first = cur
+            for a, c in zip(first, cur):
+                for x in a:
+                    assert torch.equal(a[x], c[x]), (threads, order, x)
+        for x in S.keys[0]:
+            assert torch.equal(first[0][x], ref[0][x]), x
+        for k in range(3):
+            for x in S.keys[k]:
+                assert rel(first[k][x], generic[k][x]) <= 1e-6, (k, x)
+                assert rel(first[k][x], ref[k][x]) <= 1e-6, (k, x)
+    finally:
+        S.close()
+
+
 def test_output_subsets_and_input_updates():
     """Per-disc output subsets (some discs only g_r of the gas, one disc
     nothing of the dust); rewriting the bound inputs changes the next solve."""
@@ -247,6 +284,8 @@ def test_full_batch_workload():
         with S.batch(autotune=True) as b:
             cfg = b.config()
             assert cfg["autotuned"] and cfg["tuned_ms"] > 0
+            tried = b.tune_results()
+            assert len(tried) >= 4 and min(ms for _, ms in tried) == pytest.approx(cfg["tuned_ms"])
             b.solve()
             b.sync()
             got = [{x: o[x].clone() for x in o} for o in S.out]
