@@ -35,6 +35,7 @@ METRIC = "SG field cells/s and HBM roofline fraction at rel-L2<=1e-5 vs FP64 ora
 UNIT = "cells/s"
 L2_FLUSH_BYTES = 256 << 20
 PROFILE = os.path.join(ROOT, "profiles", "cols_2048x4096.md")
+BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_64discs.md")
 
 
 def parse():
@@ -52,7 +53,7 @@ def parse():
                     help="64 uneven gas + dust discs per step instead of one 2048 x 4096 disc")
     ap.add_argument("--batch-n", type=int, default=64, help="discs in the batch (the first n of the 64)")
     ap.add_argument("--batch-config", default="auto",
-                    help="'auto' (autotune) or threads,ctas_per_sm,order (e.g. 256,2,staged)")
+                    help="'auto' (autotune) or threads,ctas_per_sm,order,specialize (e.g. 256,2,staged,1)")
     ap.add_argument("--no-loop", action="store_true", help="batch mode: skip timing the per-disc loops")
     return ap.parse_args()
 
@@ -142,9 +143,9 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(names=("sg_kernels.cu", "sg_fft.cuh", "sg_mem.cuh")):
     h = hashlib.sha256()
-    for name in ("sg_kernels.cu", "sg_fft.cuh"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2506_10812_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -160,6 +161,20 @@ def profiled_traffic():
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     if not (m and t) or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def batch_profiled_ratio():
+    """DRAM bytes per model byte of the persistent batch kernel, from the
+    committed ncu summary of a smaller batch (same kernel source)."""
+    try:
+        txt = open(BATCH_PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_model_byte:\s*([0-9.eE+]+)", txt)
+    if not (m and t) or m.group(1) != kernel_source_hash(("sg_batch.cu", "sg_fft.cuh", "sg_mem.cuh")):
         return None
     return float(t.group(1))
 
@@ -403,8 +418,9 @@ def run_batch(args):
     if args.batch_config == "auto":
         batch = Batch(plans, sg, sd, outs, autotune=True)
     else:
-        th, cps, order = args.batch_config.split(",")
-        batch = Batch(plans, sg, sd, outs, threads=int(th), ctas_per_sm=int(cps), order=order)
+        th, cps, order, spec = args.batch_config.split(",")
+        batch = Batch(plans, sg, sd, outs, threads=int(th), ctas_per_sm=int(cps), order=order,
+                      specialize=spec == "1")
     tune_ms = (time.perf_counter() - t0) * 1e3
     cfg = batch.config()
     tried = batch.tune_results()
@@ -447,6 +463,7 @@ def run_batch(args):
     model = sum(step_model_bytes(d.nr, d.nphi, 2, 6) for d in discs)
     peak, peak_kind = measured_peaks()
     achieved = model / (ms_graph * 1e-3) / 1e9
+    ratio = batch_profiled_ratio()
     from collections import Counter
     shapes = Counter(f"{d.nr}x{d.nphi}" for d in discs)
     result = {"metric": METRIC, "value": cells / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
@@ -462,7 +479,9 @@ def run_batch(args):
               "autotune_candidates": [dict(c, ms=round(m, 4)) for c, m in tried],
               "roofline": {"bound": "hbm", "kernel": "k_batch (persistent, whole step)",
                            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                           "frac": round(achieved / peak, 4), "traffic": None,
+                           "frac": round(achieved / peak, 4),
+                           "traffic": None if ratio is None else round(ratio * model),
+                           "traffic_note": "DRAM bytes of a 16-disc capture scaled by model bytes",
                            "peak_source": f"{peak_kind} HBM copy bandwidth",
                            "algorithmic_bytes_per_launch": model},
               "per_disc_loop": {"c_ms_per_step": ms_loop_c, "python_ms_per_step": ms_loop_py,
