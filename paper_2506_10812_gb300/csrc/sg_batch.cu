@@ -47,9 +47,9 @@ enum { TASK_FWD = 0, TASK_COL0 = 1, TASK_COL = 2, TASK_INV = 3 };
 template <typename R>
 struct BatchDisc {
     const R *s[2];                 // sources [nr][nphi]
-    cplx<R> *sh;                   // row spectra, [nsrc][N][nr] column-blocked
+    cplx<R> *sh;                   // row spectra, [nsrc][N][nr] (sg_mem.cuh layout)
     const cplx<R> *tab;            // kernel spectra of the plan
-    cplx<R> *oh;                   // column-pass output, [6][N][nr] column-blocked
+    cplx<R> *oh;                   // column-pass output, [6][N][nr] (sg_mem.cuh layout)
     R *out[6];                     // outputs by slot 3 b + c (NULL: not requested)
     const R *rcen;                 // r_i
     const cplx<R> *tw_row, *twp_row, *twp_col;
@@ -400,7 +400,7 @@ __device__ void prefetch_task(const BatchDisc<R> &D, int4 tk, int threads)
                 if (tk.x == TASK_COL0) prefetch_l2(t0 + (size_t)N * P, (unsigned)(P * sizeof(C)));
             }
         }
-        const int b0 = m0 >> 2, b1 = (m0 + cols - 1) >> 2;
+        const int b0 = m0 / BW, b1 = (m0 + cols - 1) / BW;
         for (int a = 0; a < ns; ++a)
             prefetch_l2(D.sh + (size_t)a * N * nr + (size_t)b0 * nr * BW,
                         (unsigned)((size_t)(b1 - b0 + 1) * nr * BW * sizeof(C)));

@@ -36,7 +36,7 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 
 // Row R2C of `nsrc` real [nrows][nphi] arrays x[a] (each row times
 // rscale[row] when rscale != NULL; row mean removed when dc) into packed
-// spectra xh + a * (nphi/2) * nrows, column-blocked [nphi/2][nrows]
+// spectra xh + a * (nphi/2) * nrows, [nphi/2][nrows] in the layout of sg_mem.cuh
 // (slot m = 0 packs the real m = 0 and m = nphi/2 coefficients).
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
@@ -50,7 +50,7 @@ template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
                         uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s);
 
-// Column FFT of a table's row spectra (column-blocked [nphi/2][L] complex
+// Column FFT of a table's row spectra ([nphi/2][L] complex, sg_mem.cuh layout,
 // double) and packing into [nphi/2 + 1][tab_pitch(L/2)] complex of type R;
 // `odd` for the sin(psi) component (stored multiplied by i).
 template <typename R>

@@ -6,7 +6,7 @@
 //   rows_fwd  each source Sigma_a [nr][nphi], scaled by r_i (see below) and
 //             with its row mean removed -> row R2C (length nphi) -> packed
 //             spectra (column m = 0 holds the real m = 0 and m = nphi/2
-//             coefficients as re + i im) stored column-blocked;
+//             coefficients as re + i im) stored column-major;
 //   cols      per column m: zero-padded length-L forward FFT of every
 //             source, products with the kernel spectra (staged in shared
 //             memory by TMA bulk copies issued at kernel start) summed over
@@ -14,9 +14,14 @@
 //             requested (target, component), rows 0..nr-1 written back;
 //   rows_inv  per output row: packed C2R (length nphi) and the epilogue.
 //
-// Column-blocked layout of the [N][rows] intermediates: element (m, i) at
-// ((m / 4) rows + i) 4 + m % 4, so a row transform that owns 4 consecutive
-// rows moves whole 128-byte lines, and a column is a stride-4 vector.
+// Layout of the [N][rows] intermediates (sg_mem.cuh, BW = 1): column-major,
+// element (m, i) at m rows + i, so the column pass moves contiguous columns
+// and a row transform that owns 4 consecutive rows moves a 32-byte slice of
+// every column.  (The column-blocked variant BW = 4, element (m, i) at
+// ((m / 4) rows + i) 4 + m % 4, gives the row transforms whole 128-byte
+// lines but makes every column access a stride-4 vector; on the 2048 x 4096
+// disc it makes the column pass 44 % slower and the row transforms 14 %
+// faster.)
 //
 // Radial scaling: the lattice kernels carry e^{-3 Delta / 2}, which makes
 // the convolution output span (r_out / r_in)^{3/2} across the grid while
@@ -44,14 +49,22 @@ namespace sg {
 
 
 // ----------------------------------------------------------------- sizes
-int row_rpc(int nphi, bool f64)
+// Rows per CTA of the row transforms: up to SG_ROW_RPC (4; 8 measured
+// slower: 1024-thread CTAs with 139 KB of shared memory), at most 1024
+// threads (nphi / 32 per row) and 160 KB of shared memory.
+#ifndef SG_ROW_RPC
+#define SG_ROW_RPC 4
+#endif
+__host__ __device__ constexpr int row_rpc_of(int nphi, int esz)
 {
-    const int T = nphi / 32;                  // threads per row transform
-    const size_t esz = f64 ? 16 : 8;
-    int rpc = 4;
-    while (rpc > 1 && (T * rpc > 512 || (size_t)rpc * padded_len(nphi / 2) * esz > 160 * 1024)) rpc >>= 1;
+    int rpc = SG_ROW_RPC;
+    while (rpc > 1 && ((nphi / 32) * rpc > 1024 || (long long)rpc * padded_len(nphi / 2) * esz > 160 * 1024))
+        rpc >>= 1;
     return rpc;
 }
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x >> 1); }
+
+int row_rpc(int nphi, bool f64) { return row_rpc_of(nphi, f64 ? 16 : 8); }
 
 size_t row_smem_bytes(int nphi, int rpc, bool f64)
 {
@@ -142,7 +155,7 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 // the row mean before the transform.
 // NC > 0: compile-time row transform length (nphi / 2).
 template <typename R, int NC>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(1024, 1)
 k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restrict__ xh, int nrows,
            int nphi_rt, int rpc, const cplx<R> *__restrict__ tw, const cplx<R> *__restrict__ twp,
            const R *__restrict__ rscale, int dc)
@@ -153,7 +166,8 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
     C *sm = reinterpret_cast<C *>(smem_raw + 64 * sizeof(double));
     const int nphi = NC > 0 ? 2 * NC : nphi_rt;
     const int N = nphi >> 1, T = N >> 4;
-    if (NC > 0) rpc = 4;                                        // row_rpc(2 NC) for NC <= 2048
+    if (NC > 0) rpc = row_rpc_of(2 * NC, sizeof(C));           // compile-time for the hot lengths
+    const int lg = ilog2(rpc);
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int a = blockIdx.y;
     const int i0 = blockIdx.x * rpc;
@@ -206,10 +220,10 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
             v[e] = cadd(E, cmul(O, __ldg(&tw[k])));
         }
     }
-    // column-blocked write through a [N][rpc] tile: rpc rows x 4 columns per line
+    // write through a [N][rpc] tile: rpc consecutive rows of each column (x BW columns)
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 16; ++e) sm[tile_idx<C>(t + T * e, g, rpc)] = v[e];
+    for (int e = 0; e < 16; ++e) sm[tile_idx_g<C>(t + T * e, g, lg)] = v[e];
     __syncthreads();
     C *out = xh + (size_t)a * N * nrows;
     const int per = rpc * BW;
@@ -217,7 +231,7 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
     for (int idx = threadIdx.x; idx < N * rpc; idx += blockDim.x) {
         const int bb = idx / per, rem = idx - bb * per;
         const int gg = rem / BW, c = rem - gg * BW;
-        st_hint(out + ((size_t)bb * nrows + i0 + gg) * BW + c, sm[tile_idx<C>(bb * BW + c, gg, rpc)], pl);
+        st_hint(out + ((size_t)bb * nrows + i0 + gg) * BW + c, sm[tile_idx_g<C>(bb * BW + c, gg, lg)], pl);
     }
 }
 
@@ -470,7 +484,7 @@ cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int n
 }
 
 // ------------------------------------------- table column FFT + packing
-// spec: column-blocked [nphi/2][L] row spectra of one real table (FP64);
+// spec: [nphi/2][L] row spectra of one real table (FP64, sg_mem.cuh layout);
 // tab: [nphi/2 + 1][P] kernel spectrum columns (slot k = S(k), 0 <= k <= H).
 template <typename R>
 __global__ void __launch_bounds__(512)
@@ -527,7 +541,7 @@ cudaError_t launch_tabcols(const void *spec, void *tab, int L, int nphi, bool od
 
 // ------------------------------------------------------- row C2R + epilogue
 template <typename R, int NC>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(1024, 1)
 k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int nrows, int nphi_rt, int rpc,
            const cplx<R> *__restrict__ tw, const cplx<R> *__restrict__ twp, const R *__restrict__ rcen,
            unsigned int *flag)
@@ -537,7 +551,8 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
     C *sm = reinterpret_cast<C *>(smem_raw + 64 * sizeof(double));
     const int nphi = NC > 0 ? 2 * NC : nphi_rt;
     const int N = nphi >> 1, T = N >> 4;
-    if (NC > 0) rpc = 4;                                        // row_rpc(2 NC) for NC <= 2048
+    if (NC > 0) rpc = row_rpc_of(2 * NC, sizeof(C));           // compile-time for the hot lengths
+    const int lg = ilog2(rpc);
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int q = blockIdx.y;
     const int i0 = blockIdx.x * rpc;
@@ -560,7 +575,7 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
             const int idx = threadIdx.x + j * blockDim.x;
             const int bb = idx / per, rem = idx - bb * per;
             const int gg = rem / BW, c = rem - gg * BW;
-            sm[tile_idx<C>(bb * BW + c, gg, rpc)] = tmp[j];
+            sm[tile_idx_g<C>(bb * BW + c, gg, lg)] = tmp[j];
         }
     }
     __syncthreads();
@@ -569,11 +584,11 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int k = t + T * e;
-        const C X = sm[tile_idx<C>(k, g, rpc)];
+        const C X = sm[tile_idx_g<C>(k, g, lg)];
         if (k == 0) {
             v[e] = mkc<C>(X.x + X.y, X.x - X.y);
         } else {
-            const C Xc = cconj(sm[tile_idx<C>(N - k, g, rpc)]);
+            const C Xc = cconj(sm[tile_idx_g<C>(N - k, g, lg)]);
             v[e] = cadd(cadd(X, Xc), cmul_i(cmulc(csub(X, Xc), __ldg(&tw[k]))));
         }
     }

@@ -1,5 +1,5 @@
-// Shared device helpers of the FFT path: the column-blocked layout of the
-// [N][rows] spectral intermediates, the swizzled transpose tile of the row
+// Shared device helpers of the FFT path: the layout of the [N][rows]
+// spectral intermediates, the swizzled transpose tile of the row
 // transforms, and L2 cache-policy loads and stores.
 #pragma once
 
@@ -9,7 +9,12 @@
 
 namespace sg {
 
-constexpr int BW = 4;   // columns per block of the column-blocked layout
+// Columns per block of the [N][rows] intermediates: element (m, i) at
+// ((m / BW) rows + i) BW + m % BW.  BW = 1 is plain column-major.
+#ifndef SG_BW
+#define SG_BW 1
+#endif
+constexpr int BW = SG_BW;
 
 // Swizzled [N][rpc] transpose tile: conflict-free for both the per-row
 // strided access (consecutive k, fixed row) and the blocked copy.
@@ -32,10 +37,10 @@ __device__ __forceinline__ int tile_idx_g(int k, int g, int lg)
     return (k << lg) + (g ^ ((k >> sh) & ((1 << lg) - 1)));
 }
 
-// column-blocked index of element (m, i) in a [N][nrows] intermediate
+// index of element (m, i) in a [N][nrows] intermediate
 __device__ __forceinline__ size_t blk(int m, int i, int nrows)
 {
-    return ((size_t)(m >> 2) * nrows + i) * BW + (m & (BW - 1));
+    return ((size_t)(m / BW) * nrows + i) * BW + (m & (BW - 1));
 }
 
 // ------------------------------------------------ L2 eviction policies
