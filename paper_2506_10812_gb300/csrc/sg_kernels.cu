@@ -206,15 +206,21 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
 #pragma unroll
     for (int e = 0; e < 16; ++e) xb[pidx(t + T * e)] = v[e];
     __syncthreads();
+    // FAST: compile-time length, 4 rows, column-major output (T % 16 == 0):
+    // every shared-memory and global index below is a per-thread base plus a
+    // compile-time multiple of e (or of the copy step).
+    constexpr bool FAST = NC >= 256 && BW == 1 && row_rpc_of(2 * NC, sizeof(C)) == 4;
+    // pidx(N - k) = zc0 - e (T + T/16) for k = t + T e (N, T e multiples of 16)
+    const int zc0 = (N - t) + (N >> 4) + ((-t) >> 4);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int k = t + T * e;
         const C Z = v[e];
-        if (k == 0) {
+        if (e == 0 && t == 0) {
             // (X[0], X[nphi/2]) packed; the mean only enters X[0]
             v[e] = mkc<C>(Z.x + Z.y + mean * (R)nphi, Z.x - Z.y);
         } else {
-            const C Zc = cconj(xb[pidx(N - k)]);
+            const C Zc = cconj(xb[FAST ? zc0 - e * (T + T / 16) : pidx(N - k)]);
             const C E = cscale(cadd(Z, Zc), (R)0.5);
             const C O = cscale(cmul_mi(csub(Z, Zc)), (R)0.5);
             v[e] = cadd(E, cmul(O, __ldg(&tw[k])));
@@ -222,16 +228,31 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
     }
     // write through a [N][rpc] tile: rpc consecutive rows of each column (x BW columns)
     __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 16; ++e) sm[tile_idx_g<C>(t + T * e, g, lg)] = v[e];
-    __syncthreads();
     C *out = xh + (size_t)a * N * nrows;
-    const int per = rpc * BW;
     const uint64_t pl = l2_evict_last();
-    for (int idx = threadIdx.x; idx < N * rpc; idx += blockDim.x) {
-        const int bb = idx / per, rem = idx - bb * per;
-        const int gg = rem / BW, c = rem - gg * BW;
-        st_hint(out + ((size_t)bb * nrows + i0 + gg) * BW + c, sm[tile_idx_g<C>(bb * BW + c, gg, lg)], pl);
+    if constexpr (FAST) {
+        // tile_idx_g(t + T e, g, 2) = 4 (t + T e) + (g ^ ((t >> 2) & 3))
+        const int tb0 = 4 * t + (g ^ ((t >> 2) & 3));
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sm[tb0 + 4 * T * e] = v[e];
+        __syncthreads();
+        // copy step j: column m = (x >> 2) + j nthr / 4, row gg = x & 3 (x = threadIdx.x)
+        constexpr int nthr = (NC / 16) * 4;
+        const int x = threadIdx.x, gg = x & 3, m0 = x >> 2;
+        const int sb0 = 4 * m0 + (gg ^ ((m0 >> 2) & 3));          // (m >> 2) & 3 is the same for every j
+        C *o0 = out + (size_t)m0 * nrows + i0 + gg;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) st_hint(o0 + (size_t)j * (nthr / 4) * nrows, sm[sb0 + j * nthr], pl);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sm[tile_idx_g<C>(t + T * e, g, lg)] = v[e];
+        __syncthreads();
+        const int per = rpc * BW;
+        for (int idx = threadIdx.x; idx < N * rpc; idx += blockDim.x) {
+            const int bb = idx / per, rem = idx - bb * per;
+            const int gg = rem / BW, c = rem - gg * BW;
+            st_hint(out + ((size_t)bb * nrows + i0 + gg) * BW + c, sm[tile_idx_g<C>(bb * BW + c, gg, lg)], pl);
+        }
     }
 }
 
@@ -557,11 +578,24 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
     const int q = blockIdx.y;
     const int i0 = blockIdx.x * rpc;
     const C *src = oh + (size_t)o.src[q] * N * nrows;
-    const int per = rpc * BW;
-    {
+    // FAST: as in k_rows_fwd, per-thread bases plus compile-time offsets
+    constexpr bool FAST = NC >= 256 && BW == 1 && row_rpc_of(2 * NC, sizeof(C)) == 4;
+    const uint64_t pf = l2_evict_first();
+    if constexpr (FAST) {
+        // copy step j: column m = (x >> 2) + j nthr / 4, row gg = x & 3; all 16 loads first
+        constexpr int nthr = (NC / 16) * 4;
+        const int x = threadIdx.x, gg = x & 3, m0 = x >> 2;
+        const C *s0 = src + (size_t)m0 * nrows + i0 + gg;
+        C tmp[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tmp[j] = ld_hint(s0 + (size_t)j * (nthr / 4) * nrows, pf);
+        const int sb0 = 4 * m0 + (gg ^ ((m0 >> 2) & 3));
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sm[sb0 + j * nthr] = tmp[j];
+    } else {
         // every thread copies exactly N rpc / blockDim = 16 elements: issue
         // all 16 loads before the first shared-memory store
-        const uint64_t pf = l2_evict_first();
+        const int per = rpc * BW;
         C tmp[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -580,15 +614,19 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
     }
     __syncthreads();
     // Z'[k] = (X[k] + X*[N-k]) + i (X[k] - X*[N-k]) W^-k  (= 2 Z[k])
+    // FAST: tile_idx_g(k, g, 2) = 4 k + (g ^ ((t >> 2) & 3)) and
+    // tile_idx_g(N - k, g, 2) = 4 (N - k) + (g ^ (((-t) >> 2) & 3)) for k = t + T e
+    const int xa0 = 4 * t + (g ^ ((t >> 2) & 3));
+    const int xc0 = 4 * (N - t) + (g ^ (((-t) >> 2) & 3));
     C v[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int k = t + T * e;
-        const C X = sm[tile_idx_g<C>(k, g, lg)];
-        if (k == 0) {
+        const C X = sm[FAST ? xa0 + 4 * T * e : tile_idx_g<C>(k, g, lg)];
+        if (e == 0 && t == 0) {
             v[e] = mkc<C>(X.x + X.y, X.x - X.y);
         } else {
-            const C Xc = cconj(sm[tile_idx_g<C>(N - k, g, lg)]);
+            const C Xc = cconj(sm[FAST ? xc0 - 4 * T * e : tile_idx_g<C>(N - k, g, lg)]);
             v[e] = cadd(cadd(X, Xc), cmul_i(cmulc(csub(X, Xc), __ldg(&tw[k]))));
         }
     }
@@ -600,14 +638,17 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
     // own r_i prefactor cancels it
     const R sc = o.is_phi[q] ? (R)1 : (R)1 / rcen[i];
     C *out = reinterpret_cast<C *>(reinterpret_cast<R *>(o.ptr[q]) + (size_t)i * nphi);
-    bool bad = false;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
-        const C y = mkc<C>(v[e].x * sc, v[e].y * sc);   // (y[2n], y[2n+1])
-        bad |= !(isfinite(y.x) && isfinite(y.y));
-        out[t + T * e] = y;
+        v[e] = mkc<C>(v[e].x * sc, v[e].y * sc);   // (y[2n], y[2n+1])
+        out[t + T * e] = v[e];
     }
-    if (flag && bad) atomicOr(flag, 1u);
+    if (flag) {
+        bool bad = false;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) bad |= !(isfinite(v[e].x) && isfinite(v[e].y));
+        if (bad) atomicOr(flag, 1u);
+    }
 }
 
 template <typename R>
