@@ -46,6 +46,9 @@ void free_all(sg_plan *pl)
                     pl->stage, pl->ipart};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    for (cudaEvent_t ev : pl->cev)
+        if (ev) cudaEventDestroy(ev);
+    if (pl->cstream) cudaStreamDestroy(pl->cstream);
     // leave no error state behind for the next call's launch check
     cudaGetLastError();
 }
@@ -268,6 +271,69 @@ sg_status solve_any(sg_plan *pl, const void *sg_, const void *sd_, void *const o
     return pl->f64 ? solve_t<double>(pl, sg_, sd_, outs, s) : solve_t<float>(pl, sg_, sd_, outs, s);
 }
 
+// Pipelined host-buffer FFT solve: row chunks of the inputs are copied on the
+// plan's copy stream while the previous chunk's row transforms run on `s`;
+// after the column pass, each chunk's inverse row transforms are followed on
+// the copy stream by that chunk's output copies, overlapping the next
+// chunk's transforms.
+template <typename R>
+sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *const host_out[6], cudaStream_t s)
+{
+    const int nr = pl->p.nr, nphi = pl->p.nphi;
+    const size_t row_b = (size_t)nphi * pl->esz, bytes = (size_t)nr * row_b;
+    char *stg = (char *)pl->stage;
+    R *dsg = (R *)stg, *dsd = pl->nsrc == 2 ? (R *)(stg + bytes) : nullptr;
+    void *dev_out[6];
+    for (int q = 0; q < 6; ++q) dev_out[q] = host_out[q] ? stg + (2 + q) * bytes : nullptr;
+    const uint32_t mask = outmask_of(pl, dev_out);
+    const int rpc = row_rpc(nphi, pl->f64);
+    const int nch = nr / rpc < 8 ? nr / rpc : 8, rows = nr / nch;
+    cudaStream_t c = pl->cstream;
+    cudaEvent_t *ein = pl->cev, *eout = pl->cev + 8, start = pl->cev[16];
+    unsigned int *flag = (pl->p.flags & SG_CHECK_FINITE) ? pl->flag : nullptr;
+    cudaError_t e = cudaEventRecord(start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c, start, 0);
+    for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+        const size_t off = (size_t)k * rows * row_b, len = (size_t)rows * row_b;
+        e = cudaMemcpyAsync((char *)dsg + off, (const char *)hsg + off, len, cudaMemcpyHostToDevice, c);
+        if (e == cudaSuccess && dsd)
+            e = cudaMemcpyAsync((char *)dsd + off, (const char *)hsd + off, len, cudaMemcpyHostToDevice, c);
+        if (e == cudaSuccess) e = cudaEventRecord(ein[k], c);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ein[k], 0);
+        if (e == cudaSuccess)
+            e = launch_rows_fwd<R>(dsg, dsd, pl->nsrc, pl->sh, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen,
+                                   true, s, k * rows, rows);
+    }
+    if (e != cudaSuccess) return cuda_fail(pl, e, "pipelined input and row transform");
+    if (!mask) return cuda_fail(pl, cudaStreamSynchronize(s), "solve");
+    e = launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
+    if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
+    RowOut ro{};
+    for (int q = 0; q < 6; ++q) {
+        if (!((mask >> q) & 1u)) continue;
+        ro.ptr[ro.n] = dev_out[q];
+        ro.src[ro.n] = q;
+        ro.is_phi[ro.n] = (q % 3) == SG_COMP_PHI;
+        ++ro.n;
+    }
+    for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+        e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, k * rows,
+                               rows);
+        if (e == cudaSuccess) e = cudaEventRecord(eout[k], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c, eout[k], 0);
+        const size_t off = (size_t)k * rows * row_b, len = (size_t)rows * row_b;
+        for (int q = 0; q < 6 && e == cudaSuccess; ++q)
+            if ((mask >> q) & 1u)
+                e = cudaMemcpyAsync((char *)host_out[q] + off, (const char *)dev_out[q] + off, len,
+                                    cudaMemcpyDeviceToHost, c);
+    }
+    if (e != cudaSuccess) return cuda_fail(pl, e, "pipelined inverse transform and output");
+    e = cudaStreamSynchronize(c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(pl, e, "solve");
+    return SG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -460,8 +526,16 @@ sg_status sg_solve_host(sg_plan *pl, const void *sigma_g, const void *sigma_d, v
             return cuda_fail(pl, e, "staging buffers");
         }
     }
+    if (!pl->cstream) {
+        e = cudaStreamCreateWithFlags(&pl->cstream, cudaStreamNonBlocking);
+        for (int i = 0; i < 17 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->cev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(pl, e, "copy stream");
+    }
     char *stg = (char *)pl->stage;
     void *host_out[6] = {phi_g, gr_g, gphi_g, phi_d, gr_d, gphi_d};
+    if (pl->p.method == SG_METHOD_FFT)
+        return pl->f64 ? solve_host_fft<double>(pl, sigma_g, sigma_d, host_out, s)
+                       : solve_host_fft<float>(pl, sigma_g, sigma_d, host_out, s);
     void *dev_out[6];
     for (int q = 0; q < 6; ++q) dev_out[q] = host_out[q] ? stg + (2 + q) * bytes : nullptr;
     e = cudaMemcpyAsync(stg, sigma_g, bytes, cudaMemcpyHostToDevice, s);

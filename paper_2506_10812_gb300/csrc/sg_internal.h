@@ -38,9 +38,12 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 // rscale[row] when rscale != NULL; row mean removed when dc) into packed
 // spectra xh + a * (nphi/2) * nrows, [nphi/2][nrows] in the layout of sg_mem.cuh
 // (slot m = 0 packs the real m = 0 and m = nphi/2 coefficients).
+// row0, nrows_run: transform only rows row0 .. row0 + nrows_run - 1 (multiples
+// of row_rpc; nrows_run < 0: to the end); nrows stays the row stride.
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
-                            const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s);
+                            const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s,
+                            int row0 = 0, int nrows_run = -1);
 
 // Column pass of the solve: forward padded FFT of every source column,
 // products with the packed kernel spectra, inverse FFT of every requested
@@ -69,7 +72,8 @@ struct RowOut {
 // check into *flag bit 1 when flag != NULL).
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
-                            const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s);
+                            const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s, int row0 = 0,
+                            int nrows_run = -1);
 
 // Indirect term (App. E): out[2 a + {0, 1}] = (A_a, B_a) in FP64; partial
 // holds indirect_blocks(nphi) x 4 doubles.
@@ -106,6 +110,8 @@ struct sg_plan {
     unsigned int *flag = nullptr;         // bit 1: non-finite output, bit 2: staging timeout
     double *ipart = nullptr;              // indirect-term partial sums
     void *stage = nullptr;                // sg_solve_host: [2 inputs + 6 outputs][cells]
+    cudaStream_t cstream = nullptr;       // sg_solve_host: copy stream of the pipelined solve
+    cudaEvent_t cev[2 * 16] = {};         // sg_solve_host: per-chunk copy / compute events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events
     char err[256] = {0};
 };

@@ -158,7 +158,7 @@ template <typename R, int NC>
 __global__ void __launch_bounds__(1024, 1)
 k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restrict__ xh, int nrows,
            int nphi_rt, int rpc, const cplx<R> *__restrict__ tw, const cplx<R> *__restrict__ twp,
-           const R *__restrict__ rscale, int dc)
+           const R *__restrict__ rscale, int dc, int row0)
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -170,7 +170,7 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
     const int lg = ilog2(rpc);
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int a = blockIdx.y;
-    const int i0 = blockIdx.x * rpc;
+    const int i0 = row0 + blockIdx.x * rpc;
     const C *xr = reinterpret_cast<const C *>((a == 0 ? x0 : x1) + (size_t)(i0 + g) * nphi);
     C *xb = sm + g * padded_len(N);
     C v[16];
@@ -258,15 +258,17 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
 
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
-                            const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s)
+                            const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s,
+                            int row0, int nrows_run)
 {
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
-    dim3 grid(nrows / rpc, nsrc);
+    if (nrows_run < 0) nrows_run = nrows - row0;
+    dim3 grid(nrows_run / rpc, nsrc);
     auto go = [&](auto kern) {
         kern<<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
             x0, x1, (cplx<R> *)xh, nrows, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rscale,
-            dc ? 1 : 0);
+            dc ? 1 : 0, row0);
     };
     if (!f64 && nphi == 4096) go(k_rows_fwd<R, 2048>);
     else if (!f64 && nphi == 2048) go(k_rows_fwd<R, 1024>);
@@ -565,7 +567,7 @@ template <typename R, int NC>
 __global__ void __launch_bounds__(1024, 1)
 k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int nrows, int nphi_rt, int rpc,
            const cplx<R> *__restrict__ tw, const cplx<R> *__restrict__ twp, const R *__restrict__ rcen,
-           unsigned int *flag)
+           unsigned int *flag, int row0)
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -576,7 +578,7 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
     const int lg = ilog2(rpc);
     const int g = threadIdx.x / T, t = threadIdx.x - g * T;
     const int q = blockIdx.y;
-    const int i0 = blockIdx.x * rpc;
+    const int i0 = row0 + blockIdx.x * rpc;
     const C *src = oh + (size_t)o.src[q] * N * nrows;
     // FAST: as in k_rows_fwd, per-thread bases plus compile-time offsets
     constexpr bool FAST = NC >= 256 && BW == 1 && row_rpc_of(2 * NC, sizeof(C)) == 4;
@@ -653,14 +655,17 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
 
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
-                            const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s)
+                            const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s, int row0,
+                            int nrows_run)
 {
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
-    dim3 grid(nr / rpc, o.n);
+    if (nrows_run < 0) nrows_run = nr - row0;
+    dim3 grid(nrows_run / rpc, o.n);
     auto go = [&](auto kern) {
         kern<<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
-            (const cplx<R> *)oh, o, nr, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rcen, flag);
+            (const cplx<R> *)oh, o, nr, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rcen, flag,
+            row0);
     };
     if (!f64 && nphi == 4096) go(k_rows_inv<R, 2048>);
     else if (!f64 && nphi == 2048) go(k_rows_inv<R, 1024>);
@@ -690,9 +695,9 @@ cudaError_t set_smem_limits(int max_optin)
 }
 
 template cudaError_t launch_rows_fwd<float>(const float *, const float *, int, void *, int, int, const void *,
-                                            const void *, const float *, bool, cudaStream_t);
+                                            const void *, const float *, bool, cudaStream_t, int, int);
 template cudaError_t launch_rows_fwd<double>(const double *, const double *, int, void *, int, int, const void *,
-                                             const void *, const double *, bool, cudaStream_t);
+                                             const void *, const double *, bool, cudaStream_t, int, int);
 template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
                                         unsigned int *, cudaStream_t);
 template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
@@ -700,8 +705,8 @@ template cudaError_t launch_cols<double>(const void *, const void *, void *, int
 template cudaError_t launch_tabcols<float>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_tabcols<double>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const void *,
-                                            const float *, unsigned int *, cudaStream_t);
+                                            const float *, unsigned int *, cudaStream_t, int, int);
 template cudaError_t launch_rows_inv<double>(const void *, const RowOut &, int, int, const void *, const void *,
-                                             const double *, unsigned int *, cudaStream_t);
+                                             const double *, unsigned int *, cudaStream_t, int, int);
 
 }  // namespace sg

@@ -247,6 +247,35 @@ def test_potential_accel_host_and_graph_agree_with_solve():
         assert torch.equal(outb[k].cpu(), ref), k
 
 
+@pytest.mark.parametrize("nr,nphi,bif,dtype,outs", [
+    (8, 64, True, torch.float32, ("phi", "gr", "gphi")),       # 2 row chunks
+    (16, 32, False, torch.float64, ("gr",)),                    # 4 chunks, FP64, one output
+    (512, 2048, True, torch.float32, ("gphi", "phi")),          # 8 chunks, compile-time rows
+    (2048, 4096, False, torch.float32, ("phi", "gr", "gphi"))])  # the benchmark disc
+def test_solve_host_pipeline_equals_solve(nr, nphi, bif, dtype, outs):
+    """sg_solve_host copies and transforms in row chunks on two streams; the
+    per-row arithmetic is unchanged, so the result equals sg_solve bit for
+    bit (pinned and pageable host buffers)."""
+    d = inputs.ragged_noise(nr, nphi, bifluid=bif, offset=23)
+    dev = torch.device("cuda:0")
+    npdt = np.float64 if dtype == torch.float64 else np.float32
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, dtype=dtype) as plan:
+        sg = torch.tensor(d.sigma_g, dtype=dtype, device=dev)
+        sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=dtype, device=dev)
+        ref = plan.solve(sg, sd, outputs=outs)
+        torch.cuda.synchronize()
+        hg = torch.from_numpy(d.sigma_g.astype(npdt)).pin_memory()
+        hd = None if d.sigma_d is None else torch.from_numpy(d.sigma_d.astype(npdt)).pin_memory()
+        hout = {k: torch.full((nr, nphi), float("nan"), dtype=dtype).pin_memory() for k in ref}
+        plan.solve_host(hg, hd, out=hout)
+        for k in ref:
+            assert torch.equal(hout[k], ref[k].cpu()), k
+        pageable = plan.solve_host(d.sigma_g.astype(npdt), None if d.sigma_d is None else d.sigma_d.astype(npdt),
+                                   outputs=outs)
+        for k in ref:
+            assert np.array_equal(pageable[k], ref[k].cpu().numpy()), k
+
+
 def test_G_and_radial_scale():
     """Linearity in G (the table scale) and radial scale invariance (App. C):
     edges x2 leave g unchanged and double Phi."""
