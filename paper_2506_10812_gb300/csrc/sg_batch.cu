@@ -151,31 +151,52 @@ __device__ void task_fwd(const BatchDisc<R> &D, int a, int rb, unsigned char *sm
 #pragma unroll
     for (int e = 0; e < 16; ++e) xb[pidx(t + T * e)] = v[e];
     __syncthreads();
+    // fast: T a multiple of 16 and at most 16 rows (column-major layout): the
+    // mirrored index, the tile swizzle and the copy addresses are per-thread
+    // bases plus multiples of e or of the copy step (as in k_rows_fwd)
+    const bool fast = BW == 1 && (T & 15) == 0 && lg <= 4;
+    const int sh = lg < 4 ? 4 - lg : 0;
+    const int zc0 = (N - t) + (N >> 4) + ((-t) >> 4);             // pidx(N - k) = zc0 - e (T + T/16)
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int k = t + T * e;
         const C Z = v[e];
-        if (k == 0) {
+        if (e == 0 && t == 0) {
             v[e] = mkc<C>(Z.x + Z.y + mean * (R)nphi, Z.x - Z.y);
         } else {
-            const C Zc = cconj(xb[pidx(N - k)]);
+            const C Zc = cconj(xb[fast ? zc0 - e * (T + T / 16) : pidx(N - k)]);
             const C E = cscale(cadd(Z, Zc), (R)0.5);
             const C O = cscale(cmul_mi(csub(Z, Zc)), (R)0.5);
             v[e] = cadd(E, cmul(O, __ldg(&D.tw_row[k])));
         }
     }
     __syncthreads();
-#pragma unroll
-    for (int e = 0; e < 16; ++e) sm[tile_idx_g<C>(t + T * e, g, lg)] = v[e];
-    __syncthreads();
     C *out = D.sh + (size_t)a * N * nr;
-    const int per = G * BW;
     const uint64_t pl = l2_evict_last();
-    for (int idx = threadIdx.x; idx < N * G; idx += blockDim.x) {
-        const int bb = idx / per, rem = idx - bb * per;
-        const int gg = rem / BW, c = rem - gg * BW;
-        if (i0 + gg < nr)
-            st_hint(out + ((size_t)bb * nr + i0 + gg) * BW + c, sm[tile_idx_g<C>(bb * BW + c, gg, lg)], pl);
+    if (fast) {
+        const int tb0 = (t << lg) + (g ^ ((t >> sh) & (G - 1)));
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sm[tb0 + ((T * e) << lg)] = v[e];
+        __syncthreads();
+        // copy step j: column m0 + j T, row gg (N G = 16 blockDim elements)
+        const int x = threadIdx.x, gg = x & (G - 1), m0 = x >> lg;
+        const int sb0 = (m0 << lg) + (gg ^ ((m0 >> sh) & (G - 1)));
+        if (i0 + gg < nr) {
+            C *o0 = out + (size_t)m0 * nr + i0 + gg;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) st_hint(o0 + (size_t)j * T * nr, sm[sb0 + j * (int)blockDim.x], pl);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) sm[tile_idx_g<C>(t + T * e, g, lg)] = v[e];
+        __syncthreads();
+        const int per = G * BW;
+        for (int idx = threadIdx.x; idx < N * G; idx += blockDim.x) {
+            const int bb = idx / per, rem = idx - bb * per;
+            const int gg = rem / BW, c = rem - gg * BW;
+            if (i0 + gg < nr)
+                st_hint(out + ((size_t)bb * nr + i0 + gg) * BW + c, sm[tile_idx_g<C>(bb * BW + c, gg, lg)], pl);
+        }
     }
 }
 
@@ -251,6 +272,111 @@ __device__ void task_col(const BatchDisc<R> &D, int cb, unsigned char *smem)
     }
 }
 
+// Gas + dust column task with two groups per column (G = threads / T >= 2):
+// groups 2j and 2j + 1 share column m = cb G/2 + j.  Group 2j + r runs the
+// forward transform of source r into the column's shared spectrum buffer,
+// then the three outputs of target b = r.  While one output's inverse
+// transform runs, the kernel-spectrum columns of its next output (the two
+// sources' columns of pair (a, b), component c) are staged into the group's
+// shared buffer by 1-D bulk copies on the group's mbarrier.  Same products,
+// summation order and transforms as task_col.
+//
+// Shared memory per column, in complex elements (every region 16-byte
+// aligned): 2 (two mbarriers) | 2 x align2(padded_len(L)) (exchange buffers)
+// | 2 L (both spectra) | 2 x 2 P (staged kernel spectra).
+__host__ __device__ inline size_t col2_elems(int L, int P)
+{
+    const size_t xbn = (size_t)(padded_len(L) + 1) & ~(size_t)1;
+    return 2 + 2 * xbn + 2 * (size_t)L + 4 * (size_t)P;
+}
+
+template <typename R, int LC>
+__device__ void task_col2(const BatchDisc<R> &D, int cb, unsigned char *smem, unsigned *flag, bool &failed)
+{
+    using C = cplx<R>;
+    const int nr = D.nr, N = D.nphi >> 1, L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
+    const int G = blockDim.x / T, cpt = G >> 1;
+    const int g = threadIdx.x / T, t = threadIdx.x - g * T;
+    const int j = g >> 1, r = g & 1;
+    const int m = cb * cpt + j;
+    const bool valid = m >= 1 && m < N;
+    const int mv = min(max(m, 1), N - 1);
+    const size_t xbn = (size_t)(padded_len(L) + 1) & ~(size_t)1;
+    C *col = reinterpret_cast<C *>(smem) + (size_t)j * col2_elems(L, P);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(col) + r;
+    C *xb = col + 2 + r * xbn;
+    C *spec = col + 2 + 2 * xbn;
+    C *stage = spec + 2 * L + 2 * (size_t)r * P;
+    const bool leader = t == 0;
+    auto issue = [&](int c) {
+        if (leader && ((D.outmask >> (3 * r + c)) & 1u)) {
+            const uint64_t pol = l2_evict_first();
+            mbar_expect_tx(bar, 2u * P * sizeof(C));
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                tma_load_1d(stage + (size_t)a * P, D.tab + ((size_t)((a * 2 + r) * 3 + c) * (N + 1) + mv) * P,
+                            P * sizeof(C), bar, pol);
+        }
+    };
+    if (leader) {
+        mbar_init(bar, 1);
+        fence_proxy_async();                        // the stage held another task's data
+    }
+    __syncthreads();
+    issue(0);                                       // lands during the forward transform
+    const uint64_t pf = l2_evict_first();
+    C v[16];
+    {
+        const C *src = D.sh + (size_t)r * N * nr;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(src + blk(mv, t + T * e, nr), pf);
+#pragma unroll
+        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
+    }
+    fft_any<true, LC>(v, L, T, t, xb, D.twp_col);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) spec[(size_t)r * L + t + T * e] = v[e];
+    __syncthreads();                                // both spectra complete
+    const uint64_t pl = l2_evict_last();
+    unsigned ph = 0;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        const int q = 3 * r + c;
+        const bool req = (D.outmask >> q) & 1u;
+        bool ok = true;
+        if (req) ok = mbar_wait_bounded(bar, ph & 1u, flag, 4u);
+        if (__syncthreads_or(!ok)) {
+            failed = true;                          // a staged copy never landed: give up on this task
+            return;
+        }
+        if (req) ++ph;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int k = t + T * e;
+            C acc = mkc<C>(0, 0);
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                C S = e >= 8 ? cconj(stage[(size_t)a * P + 2 * H - k]) : stage[(size_t)a * P + k];
+                if (c == 2) S = cmul_mi(S);
+                acc = cfma(spec[(size_t)a * L + k], S, acc);
+            }
+            v[e] = acc;
+        }
+        __syncthreads();                            // every read of the stage precedes its rewrite
+        if (c < 2) {
+            if (leader) fence_proxy_async();
+            issue(c + 1);
+        }
+        fft_any<false, LC>(v, L, T, t, xb, D.twp_col);
+        if (valid && req) {
+            C *o = D.oh + (size_t)q * N * nr;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) st_hint(o + blk(m, t + T * e, nr), v[e], pl);
+        }
+    }
+    if (leader) mbar_inval(bar);                    // every wait on it has returned
+}
+
 // Column m = 0 (the packed m = 0 and m = nphi/2 real columns).  Every group
 // computes it; group 0 stores.  Same arithmetic as col0_path.
 template <typename R, int NS>
@@ -317,36 +443,51 @@ __device__ void task_inv(const BatchDisc<R> &D, int q, int rb, const BatchArgs &
     const int i0 = rb * G;
     const C *src = D.oh + (size_t)q * N * nr;
     const int per = G * BW;
+    // fast: as in task_fwd (per-thread bases)
+    const bool fast = BW == 1 && (T & 15) == 0 && lg <= 4;
+    const int sh = lg < 4 ? 4 - lg : 0;
     {
         // N G = 16 blockDim elements: 16 loads per thread, all issued first
         const uint64_t pf = l2_evict_first();
         C tmp[16];
+        if (fast) {
+            const int x = threadIdx.x, gg = x & (G - 1), m0 = x >> lg;
+            const C *s0 = src + (size_t)m0 * nr + min(i0 + gg, nr - 1);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int idx = threadIdx.x + j * blockDim.x;
-            const int bb = idx / per, rem = idx - bb * per;
-            const int gg = rem / BW, c = rem - gg * BW;
-            const int row = min(i0 + gg, nr - 1);
-            tmp[j] = ld_cg_hint(src + ((size_t)bb * nr + row) * BW + c, pf);
-        }
+            for (int j = 0; j < 16; ++j) tmp[j] = ld_cg_hint(s0 + (size_t)j * T * nr, pf);
+            const int sb0 = (m0 << lg) + (gg ^ ((m0 >> sh) & (G - 1)));
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int idx = threadIdx.x + j * blockDim.x;
-            const int bb = idx / per, rem = idx - bb * per;
-            const int gg = rem / BW, c = rem - gg * BW;
-            sm[tile_idx_g<C>(bb * BW + c, gg, lg)] = tmp[j];
+            for (int j = 0; j < 16; ++j) sm[sb0 + j * (int)blockDim.x] = tmp[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int idx = threadIdx.x + j * blockDim.x;
+                const int bb = idx / per, rem = idx - bb * per;
+                const int gg = rem / BW, c = rem - gg * BW;
+                const int row = min(i0 + gg, nr - 1);
+                tmp[j] = ld_cg_hint(src + ((size_t)bb * nr + row) * BW + c, pf);
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int idx = threadIdx.x + j * blockDim.x;
+                const int bb = idx / per, rem = idx - bb * per;
+                const int gg = rem / BW, c = rem - gg * BW;
+                sm[tile_idx_g<C>(bb * BW + c, gg, lg)] = tmp[j];
+            }
         }
     }
     __syncthreads();
+    const int xa0 = (t << lg) + (g ^ ((t >> sh) & (G - 1)));
+    const int xc0 = ((N - t) << lg) + (g ^ (((-t) >> sh) & (G - 1)));
     C v[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         const int k = t + T * e;
-        const C X = sm[tile_idx_g<C>(k, g, lg)];
-        if (k == 0) {
+        const C X = sm[fast ? xa0 + ((T * e) << lg) : tile_idx_g<C>(k, g, lg)];
+        if (e == 0 && t == 0) {
             v[e] = mkc<C>(X.x + X.y, X.x - X.y);
         } else {
-            const C Xc = cconj(sm[tile_idx_g<C>(N - k, g, lg)]);
+            const C Xc = cconj(sm[fast ? xc0 - ((T * e) << lg) : tile_idx_g<C>(N - k, g, lg)]);
             v[e] = cadd(cadd(X, Xc), cmul_i(cmulc(csub(X, Xc), __ldg(&D.tw_row[k]))));
         }
     }
@@ -388,7 +529,8 @@ __device__ void prefetch_task(const BatchDisc<R> &D, int4 tk, int threads)
         const int i0 = tk.w * G, rows = min(G, nr - i0);
         prefetch_l2(D.s[tk.z] + (size_t)i0 * nphi, (unsigned)((size_t)rows * nphi * sizeof(R)));
     } else if (tk.x == TASK_COL || tk.x == TASK_COL0) {
-        const int G = threads / (L >> 4);
+        const int G0 = threads / (L >> 4);
+        const int G = (ns == 2 && G0 >= 2) ? G0 / 2 : G0;             // columns per task
         const int m0 = tk.x == TASK_COL ? tk.w * G : 0;
         const int cols = tk.x == TASK_COL ? min(G, N - m0) : 1;
         for (int q = 0; q < 3 * ns; ++q) {
@@ -468,6 +610,16 @@ __global__ void __launch_bounds__(512) k_batch(const BatchDisc<R> *__restrict__ 
                 else if (SPEC && D.nr == 1024) task_col<R, 1, SPEC ? 2048 : 0>(D, tk.w, smem_raw);
                 else if (SPEC && D.nr == 512) task_col<R, 1, SPEC ? 1024 : 0>(D, tk.w, smem_raw);
                 else task_col<R, 1, 0>(D, tk.w, smem_raw);
+            } else if ((int)blockDim.x >= D.nr / 4) {      // two groups per column
+                bool failed = false;
+                if (SPEC && D.nr == 2048) task_col2<R, SPEC ? 4096 : 0>(D, tk.w, smem_raw, A.flag, failed);
+                else if (SPEC && D.nr == 1024) task_col2<R, SPEC ? 2048 : 0>(D, tk.w, smem_raw, A.flag, failed);
+                else if (SPEC && D.nr == 512) task_col2<R, SPEC ? 1024 : 0>(D, tk.w, smem_raw, A.flag, failed);
+                else task_col2<R, 0>(D, tk.w, smem_raw, A.flag, failed);
+                if (failed) {
+                    if (threadIdx.x == 0) atomicExch(A.ctl + 1, 1u);
+                    return;
+                }
             } else {
                 if (SPEC && D.nr == 2048) task_col<R, 2, SPEC ? 4096 : 0>(D, tk.w, smem_raw);
                 else if (SPEC && D.nr == 1024) task_col<R, 2, SPEC ? 2048 : 0>(D, tk.w, smem_raw);
@@ -548,6 +700,14 @@ uint32_t batch_outmask(const sg_batch *b, int k)
     return m;
 }
 
+// Columns per column task: one per group, or one per two groups for gas +
+// dust when a block holds at least two transforms (task_col2).
+int cols_per_task(const sg_plan *pl, int threads)
+{
+    const int G = threads / (2 * pl->p.nr / 16);
+    return (pl->nsrc == 2 && G >= 2) ? G / 2 : G;
+}
+
 // Dynamic shared memory of one task of disc k with `threads` threads.
 size_t task_smem(const sg_plan *pl, int threads)
 {
@@ -555,7 +715,9 @@ size_t task_smem(const sg_plan *pl, int threads)
     const int N = pl->p.nphi / 2, L = 2 * pl->p.nr;
     const int Gr = threads / (N / 16), Gc = threads / (L / 16);
     const size_t rows = 64 * sizeof(double) + (size_t)Gr * padded_len(N) * esz;
-    const size_t col = (size_t)Gc * (padded_len(L) + (pl->nsrc - 1) * 2 * L) * esz;
+    const size_t col = (pl->nsrc == 2 && Gc >= 2)
+                           ? (size_t)(Gc / 2) * col2_elems(L, tab_pitch(pl->p.nr)) * esz
+                           : (size_t)Gc * (padded_len(L) + (pl->nsrc - 1) * 2 * L) * esz;
     const size_t col0 = (size_t)Gc * (padded_len(L) + 2 * L) * esz;
     return std::max(rows, std::max(col, col0));
 }
@@ -590,7 +752,7 @@ void build_tasks(sg_batch *b, int threads, int order, std::vector<BatchDisc<R>> 
         D.nphi = nphi;
         D.nsrc = pl->nsrc;
         D.outmask = batch_outmask(b, k);
-        const int Gr = threads / (N / 16), Gc = threads / (L / 16);
+        const int Gr = threads / (N / 16), Gc = cols_per_task(pl, threads);
         const int rblocks = (nr + Gr - 1) / Gr;
         const int cblocks = (N + Gc - 1) / Gc;       // tile 0 holds column 0's group (idle) and 1..Gc-1
         for (int a = 0; a < pl->nsrc; ++a)
