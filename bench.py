@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--batch-config", default="auto",
                     help="'auto' (autotune) or threads,ctas_per_sm,order,specialize (e.g. 256,2,staged,1)")
     ap.add_argument("--no-loop", action="store_true", help="batch mode: skip timing the per-disc loops")
+    ap.add_argument("--engine", default="fft32",
+                    choices=("fft32", "dft_fp16x3", "dft_bf16x3", "dft_fp16", "dft_bf16"),
+                    help="column-pass engine (tensor-core DFT stages for the precision study; gas-only discs)")
     return ap.parse_args()
 
 
@@ -248,6 +251,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     plan = Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, device=dev)
     plan_build_ms = (time.perf_counter() - t0) * 1e3
+    if args.engine != "fft32":
+        plan.set_column_engine(args.engine)
     sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
     sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=torch.float32, device=dev)
     out = plan.solve(sg, sd)
@@ -306,8 +311,10 @@ def run_ours(args):
     col_ms = statistics.mean(stage["cols"])
     peak, peak_kind = measured_peaks()
     achieved = col_bytes / (col_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_cols (fused column pass)", "achieved": round(achieved, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(),
+    kname = "k_cols (fused column pass)" if args.engine == "fft32" else f"k_cols_mma ({args.engine} tensor-core DFT stages)"
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic() if args.engine == "fft32" else None,
                 "peak_source": f"{peak_kind} HBM copy bandwidth", "algorithmic_bytes_per_launch": col_bytes}
     # whole step against the 3-pass model traffic (60 B/cell gas-only with Phi)
     step_bytes = col_bytes + 8 * nsrc * N * nr * 2 + 4 * nsrc * d.cells + 8 * nsrc * ncomp * N * nr + 4 * nsrc * ncomp * d.cells
@@ -330,8 +337,9 @@ def run_ours(args):
 
     result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
               "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-              "dtype": "f32", "data": "synthetic (seeded log-normal disc, no dataset)",
-              "config": config_of(args, d),
+              "dtype": "f32" if args.engine == "fft32" else f"f32 ({args.engine} tensor-core column DFTs)",
+              "data": "synthetic (seeded log-normal disc, no dataset)",
+              "config": dict(config_of(args, d), **({} if args.engine == "fft32" else {"column_engine": args.engine})),
               "roofline": roofline,
               "step_roofline": {"model_bytes_per_step": step_bytes, "frac": round(step_frac, 4),
                                 "note": "3-pass traffic model over the whole step"},

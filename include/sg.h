@@ -307,6 +307,21 @@ int32_t sg_batch_tune_results(const sg_batch *batch, int32_t max, sg_batch_opts 
 void sg_batch_destroy(sg_batch *batch);
 const char *sg_batch_last_error(const sg_batch *batch);
 
+/* Column-pass engine of an FFT plan, for the precision study of the DFT
+ * stages (Sec. 5.2 FFT convolution evaluated with the DFTs on tensor cores).
+ * SG_ENGINE_FFT32 (default): the FP32 register FFT.  The others compute
+ * every radix-16 / radix-8 stage of the column transforms as a block-matrix
+ * product on the tensor cores (warp-level mma.sync, m16n8k16, FP32
+ * accumulate), with FP16 or BF16 operands split into high and low parts and
+ * three products summed (..._X3), or a single product.  They need an FP32
+ * gas-only FFT plan with nr = 1024 or 2048 (SG_ERR_UNSUPPORTED otherwise);
+ * column 0 stays on the FP32 path.  The call allocates a 4 KiB table on the
+ * first tensor-core engine and synchronises the device; set it before
+ * capturing solves in a graph.  Batches ignore it.                       */
+enum { SG_ENGINE_FFT32 = 0, SG_ENGINE_DFT_FP16X3 = 1, SG_ENGINE_DFT_BF16X3 = 2, SG_ENGINE_DFT_FP16 = 3,
+       SG_ENGINE_DFT_BF16 = 4 };
+sg_status sg_set_column_engine(sg_plan *plan, int32_t engine);
+
 /* Release a plan and all its device memory (NULL is a no-op).  Synchronises
  * the device before freeing.                                               */
 void sg_destroy(sg_plan *plan);

@@ -20,10 +20,12 @@ SG_COMP_PHI, SG_COMP_R, SG_COMP_AZ = 0, 1, 2
 SG_CHECK_FINITE = 2
 SG_BATCH_HOST_GATE = 4
 SG_BATCH_ORDER_PIPELINED, SG_BATCH_ORDER_STAGED = 0, 1
+SG_ENGINE_FFT32, SG_ENGINE_DFT_FP16X3, SG_ENGINE_DFT_BF16X3, SG_ENGINE_DFT_FP16, SG_ENGINE_DFT_BF16 = range(5)
+ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf16": 4}
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
-           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_batch_create", "sg_batch_solve",
+           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_set_column_engine", "sg_batch_create", "sg_batch_solve",
            "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_tune_results", "sg_batch_destroy",
            "sg_batch_last_error", "sg_destroy", "sg_status_string", "sg_last_error")
 
@@ -101,6 +103,8 @@ def load() -> ctypes.CDLL:
     lib.sg_batch_destroy.restype = None
     lib.sg_batch_last_error.argtypes = [vp]
     lib.sg_batch_last_error.restype = ctypes.c_char_p
+    lib.sg_set_column_engine.argtypes = [vp, i32]
+    lib.sg_set_column_engine.restype = st
     lib.sg_launches_per_solve.argtypes = [vp, u32]
     lib.sg_launches_per_solve.restype = i32
     lib.sg_destroy.argtypes = [vp]

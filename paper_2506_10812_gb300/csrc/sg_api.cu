@@ -43,7 +43,7 @@ void free_all(sg_plan *pl)
     if (pl->twp_col == pl->twp_col64) pl->twp_col = nullptr;
     void *ptrs[] = {pl->tw_row, pl->tw_row64, pl->twp_row, pl->twp_row64, pl->twp_col, pl->twp_col64,
                     pl->tab, pl->sh, pl->oh, pl->rcen, pl->geo_i, pl->geo_j, pl->Hg, pl->Hd, pl->flag,
-                    pl->stage, pl->ipart};
+                    pl->stage, pl->ipart, pl->atab};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (cudaEvent_t ev : pl->cev)
@@ -230,7 +230,9 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
                                pl->twp_row, (const R *)pl->rcen, true, s);
         if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
         if (ev) cudaEventRecord(pl->ev[1], s);
-        e = launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
+        e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
+                                         pl->flag, s)
+                       : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
         RowOut ro{};
@@ -306,7 +308,9 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     }
     if (e != cudaSuccess) return cuda_fail(pl, e, "pipelined input and row transform");
     if (!mask) return cuda_fail(pl, cudaStreamSynchronize(s), "solve");
-    e = launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
+    e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
+                                     pl->flag, s)
+                   : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
     if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
     RowOut ro{};
     for (int q = 0; q < 6; ++q) {
@@ -618,8 +622,31 @@ int32_t sg_launches_per_solve(const sg_plan *pl, uint32_t outmask)
     const uint32_t allowed = pl->nsrc == 2 ? 0x3Fu : 0x7u;
     outmask &= allowed;
     if (!outmask) return 0;
-    if (pl->p.method == SG_METHOD_FFT) return 3;
+    if (pl->p.method == SG_METHOD_FFT) return pl->engine ? 4 : 3;   // tensor-core engines: column 0 apart
     return ((outmask & 7u) ? 1 : 0) + ((outmask & 0x38u) ? 1 : 0);
+}
+
+sg_status sg_set_column_engine(sg_plan *pl, int32_t engine)
+{
+    if (!pl) return SG_ERR_ARG;
+    if (engine < SG_ENGINE_FFT32 || engine > SG_ENGINE_DFT_BF16) return fail(pl, SG_ERR_ARG, "unknown engine %d", engine);
+    if (engine == SG_ENGINE_FFT32) {
+        pl->engine = 0;
+        return SG_OK;
+    }
+    if (pl->p.method != SG_METHOD_FFT || pl->f64 || pl->nsrc != 1 || (pl->p.nr != 1024 && pl->p.nr != 2048))
+        return fail(pl, SG_ERR_UNSUPPORTED,
+                    "tensor-core column engines need an FP32 gas-only FFT plan with nr = 1024 or 2048");
+    sg_status st = check_device(pl);
+    if (st != SG_OK) return st;
+    uint32_t h[8 * 32 * 4];
+    dftmma_frag_table(engine == SG_ENGINE_DFT_FP16X3 || engine == SG_ENGINE_DFT_FP16, h);
+    cudaError_t e = cudaSuccess;
+    if (!pl->atab) e = cudaMalloc((void **)&pl->atab, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemcpy(pl->atab, h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(pl, e, "fragment table");
+    pl->engine = engine;
+    return SG_OK;
 }
 
 void sg_destroy(sg_plan *pl)

@@ -49,9 +49,19 @@ cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nr
 // products with the packed kernel spectra, inverse FFT of every requested
 // (target, component), rows 0..nr-1 kept.
 // flag: bit 2 set when a staged copy never completed (bounded wait).
+// ncols > 0: only columns 0 .. ncols - 1.
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
-                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s);
+                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols = 0);
+
+// Column pass with tensor-core DFT stages (sg_dftmma.cu): FP32 gas-only
+// plans with 2 nr in {2048, 4096}; engine 1..4 as SG_ENGINE_DFT_*; atab
+// the A-fragment table of the engine's precision (dftmma_frag_table).
+cudaError_t launch_cols_mma(int engine, const void *sh, const void *tab, void *oh, int nr, int nphi, uint32_t outmask,
+                            const void *tw_col, const uint32_t *atab, unsigned int *flag, cudaStream_t s);
+size_t cols_mma_smem(int nr);
+// Host: the 8 x 32 x 4 A-fragment words (FP16 if f16, else BF16).
+void dftmma_frag_table(bool f16, uint32_t *out);
 
 // Column FFT of a table's row spectra ([nphi/2][L] complex, sg_mem.cuh layout,
 // double) and packing into [nphi/2 + 1][tab_pitch(L/2)] complex of type R;
@@ -110,6 +120,8 @@ struct sg_plan {
     unsigned int *flag = nullptr;         // bit 1: non-finite output, bit 2: staging timeout
     double *ipart = nullptr;              // indirect-term partial sums
     void *stage = nullptr;                // sg_solve_host: [2 inputs + 6 outputs][cells]
+    int engine = 0;                       // column-pass engine (SG_ENGINE_*)
+    uint32_t *atab = nullptr;             // its A-fragment table (tensor-core engines)
     cudaStream_t cstream = nullptr;       // sg_solve_host: copy stream of the pipelined solve
     cudaEvent_t cev[2 * 16] = {};         // sg_solve_host: per-chunk copy / compute events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events

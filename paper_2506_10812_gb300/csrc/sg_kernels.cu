@@ -439,13 +439,14 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
 
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
-                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s)
+                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols)
 {
     const bool f64 = sizeof(R) == 8;
     const int N = nphi / 2, T = (2 * nr) / 16;
     const size_t smem = col_smem_bytes(nr, nsrc, f64);
+    const int grid = ncols > 0 && ncols < N ? ncols : N;
     auto go = [&](auto kern) {
-        kern<<<N, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N, outmask,
+        kern<<<grid, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N, outmask,
                                 (const cplx<R> *)tw_col, flag);
     };
     const int L = 2 * nr;
@@ -654,9 +655,9 @@ template cudaError_t launch_rows_fwd<float>(const float *, const float *, int, v
 template cudaError_t launch_rows_fwd<double>(const double *, const double *, int, void *, int, int, const void *,
                                              const void *, const double *, bool, cudaStream_t, int, int);
 template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
-                                        unsigned int *, cudaStream_t);
+                                        unsigned int *, cudaStream_t, int);
 template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
-                                         unsigned int *, cudaStream_t);
+                                         unsigned int *, cudaStream_t, int);
 template cudaError_t launch_tabcols<float>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_tabcols<double>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const void *,

@@ -183,6 +183,13 @@ class Plan:
         N.check(st, self._h, "sg_solve_host")
         return out
 
+    def set_column_engine(self, engine):
+        """Column-pass engine: "fft32" (default) or a tensor-core DFT engine
+        ("dft_fp16x3", "dft_bf16x3", "dft_fp16", "dft_bf16")."""
+        with torch.cuda.device(self.device):
+            st = self._lib.sg_set_column_engine(self._h, N.ENGINES[engine])
+        N.check(st, self._h, "sg_set_column_engine")
+
     def sync(self):
         with torch.cuda.device(self.device):
             st = self._lib.sg_sync(self._h, self._stream())

@@ -1,0 +1,108 @@
+"""GPU tests of the tensor-core column engines (split-precision DFT-as-GEMM
+stages, the precision study of the FFT path): error against the FP64 oracle
+on the precision-study discs, agreement with the FP32 FFT engine, the
+single-term modes' larger error, and the engine's argument checks."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_10812_gb300 import _native as N
+from paper_2506_10812_gb300 import build as B
+from paper_2506_10812_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = (1e-5, 1e-4)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    B.build()
+    N.load()
+    oracle.build()
+
+
+def rounded(d):
+    import copy
+    e = copy.copy(d)
+    e.sigma_g = d.sigma_g.astype(np.float32).astype(np.float64)
+    return e
+
+
+def solve(d, engine):
+    from paper_2506_10812_gb300 import Plan
+    dev = torch.device("cuda:0")
+    with Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, None, G=d.G, device=dev) as plan:
+        plan.set_column_engine(engine)
+        assert plan.launches_per_solve() == (3 if engine == "fft32" else 4)
+        sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
+        out = plan.solve(sg)
+        plan.sync()
+        return {k: v.double().cpu().numpy() for k, v in out.items()}
+
+
+def errors(out, ref):
+    return {k: (oracle.rel_l2(v, ref[k]), oracle.rel_max(v, ref[k])) for k, v in out.items()}
+
+
+@pytest.fixture(scope="module")
+def disc_1024():
+    d = rounded(inputs.lognormal_gas(1024, 2048))
+    ref = oracle.fft64(oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out), d.sigma_g, h_g=d.h_g, G=d.G)
+    return d, ref
+
+
+def test_fp16x3_meets_fp32_tolerance(disc_1024):
+    """FP16 hi + lo operands, three products, FP32 accumulation: the FP32
+    tolerance against the FP64 oracle (Phi, g_r, g_phi)."""
+    d, ref = disc_1024
+    err = errors(solve(d, "dft_fp16x3"), ref)
+    for k, (e2, em) in err.items():
+        assert e2 <= TOL32[0] and em <= TOL32[1], (k, e2, em)
+
+
+def test_engines_against_fft32_and_oracle(disc_1024):
+    """Every engine against the FP32 FFT engine and the oracle: the split
+    modes stay within 10x the FP32 tolerance of the oracle; a single FP16 or
+    BF16 product is orders of magnitude worse (what the split recovers)."""
+    d, ref = disc_1024
+    base = errors(solve(d, "fft32"), ref)
+    for k, (e2, em) in base.items():
+        assert e2 <= TOL32[0] and em <= TOL32[1], ("fft32", k, e2, em)
+    split = {e: errors(solve(d, e), ref) for e in ("dft_fp16x3", "dft_bf16x3")}
+    single = {e: errors(solve(d, e), ref) for e in ("dft_fp16", "dft_bf16")}
+    for e, err in split.items():
+        for k, (e2, em) in err.items():
+            assert e2 <= 10 * TOL32[0] and em <= 10 * TOL32[1], (e, k, e2, em)
+    for e, err in single.items():
+        worst = max(e2 for e2, _ in err.values())
+        assert worst > 10 * max(max(e2 for e2, _ in s.values()) for s in split.values()), (e, err)
+
+
+def test_fp16x3_full_size():
+    """2048 x 4096 (column length 4096: three radix-16 stages)."""
+    d = rounded(inputs.lognormal_gas(2048, 4096))
+    ref = oracle.fft64(oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out), d.sigma_g, h_g=d.h_g, G=d.G)
+    err = errors(solve(d, "dft_fp16x3"), ref)
+    for k, (e2, em) in err.items():
+        assert e2 <= TOL32[0] and em <= TOL32[1], (k, e2, em)
+
+
+def test_engine_argument_checks():
+    from paper_2506_10812_gb300 import Plan
+    dev = torch.device("cuda:0")
+    d = inputs.ragged_noise(512, 64)
+    with Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, None, device=dev) as plan:
+        with pytest.raises(N.SgError) as ei:
+            plan.set_column_engine("dft_fp16x3")             # nr = 512
+        assert ei.value.status == N.SG_ERR_UNSUPPORTED
+        assert plan._lib.sg_set_column_engine(plan._h, 9) == N.SG_ERR_ARG
+    with Plan(1024, 64, 0.1, 5.0, 0.05, 0.01, device=dev) as plan:  # gas + dust
+        with pytest.raises(N.SgError) as ei:
+            plan.set_column_engine("dft_bf16x3")
+        assert ei.value.status == N.SG_ERR_UNSUPPORTED
+    with Plan(1024, 64, 0.1, 5.0, 0.05, dtype=torch.float64, device=dev) as plan:
+        with pytest.raises(N.SgError) as ei:
+            plan.set_column_engine("dft_fp16")
+        assert ei.value.status == N.SG_ERR_UNSUPPORTED
