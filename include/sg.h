@@ -322,6 +322,80 @@ enum { SG_ENGINE_FFT32 = 0, SG_ENGINE_DFT_FP16X3 = 1, SG_ENGINE_DFT_BF16X3 = 2, 
        SG_ENGINE_DFT_BF16 = 4 };
 sg_status sg_set_column_engine(sg_plan *plan, int32_t engine);
 
+/* ------------------------------------------------------------------------
+ * Kernels of the spectral neural-operator surrogate of the field solve
+ * (paper_2506_10812_gb300/surrogate.py builds a 4-layer, width-32 spectral
+ * neural operator from them, trains it on fields the FFT solve labels and
+ * gates it against that exact path).  Every pointer is a caller-owned
+ * device buffer, row-major; "bf16" buffers hold bfloat16, the others float.
+ * Each call enqueues on `stream` and returns SG_ERR_ARG for NULL or
+ * non-positive sizes, SG_ERR_CUDA for a launch error.
+ * ---------------------------------------------------------------------- */
+
+/* Batched GEMM on the tensor cores (mma.sync m16n8k16, bf16 in, FP32
+ * accumulate): for z < batch,
+ *   C[z] = alpha op(A[z]) B[z] + beta C[z] (+ bias[n]),
+ * op(A) = A ([M][K], leading dim lda) or, with trans_a, A^T (A stored [K][M]);
+ * B [K][N] (ldb); C [M][N] (ldc) float and/or C_bf16 (same layout, bf16);
+ * stride_* are batch strides in elements (0 broadcasts); bias float [N] or
+ * NULL; beta != 0 needs C.  batch <= 65535.                               */
+sg_status sg_nn_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, float alpha, const void *A, int32_t lda,
+                     int64_t stride_a, int32_t trans_a, const void *B, int32_t ldb, int64_t stride_b, float beta,
+                     float *C, int32_t ldc, int64_t stride_c, void *C_bf16, const float *bias, void *stream);
+
+/* Radial-DFT combine of a spectral convolution: T [B][2 K1][2 M1][C] float
+ * (rows < K1: cosine rows, >= K1: minus-sine rows; column 2m + {re, im}) ->
+ * V2 [B][K1][M1][C] complex (float2) = (Gc + i Gs)(V1r + i V1i).  _bwd maps
+ * the complex gradient dV2 to dT (bf16, same layout as T).              */
+sg_status sg_nn_spec_combine(int32_t B, int32_t K1, int32_t M1, int32_t C, const float *T, void *V2, void *stream);
+sg_status sg_nn_spec_combine_bwd(int32_t B, int32_t K1, int32_t M1, int32_t C, const void *dV2, void *dT_bf16,
+                                 void *stream);
+
+/* Per-mode complex channel mixing: O[b][kk][m][o] = sum_i V2[b][kk][m][i]
+ * W[kk][m][i][o] (float2), written as bf16 planes O[b][re, im][kk][m][o].
+ * _bwd: from dO (float planes, same layout) the gradients dV2 = dO conj(W)
+ * and dW = sum_b conj(V2) dO (either output may be NULL).                */
+sg_status sg_nn_modemix(int32_t B, int32_t K1, int32_t M1, int32_t C, const void *V2, const void *W, void *O_bf16,
+                        void *stream);
+sg_status sg_nn_modemix_bwd(int32_t B, int32_t K1, int32_t M1, int32_t C, const void *V2, const void *W,
+                            const float *dO, void *dV2, void *dW, void *stream);
+
+/* y = GELU(x) (gelu_on) or x, float -> bf16; _bwd: dpre = dy GELU'(pre) (or
+ * dy) as float and/or bf16.                                             */
+sg_status sg_nn_act(int64_t n, const float *x, void *y_bf16, int32_t gelu_on, void *stream);
+sg_status sg_nn_act_bwd(int64_t n, const float *pre, const float *dy, float *dpre, void *dpre_bf16, int32_t gelu_on,
+                        void *stream);
+/* out[c] (+)= sum_r x[r][c] for x [rows][C].                            */
+sg_status sg_nn_colsum(int64_t rows, int32_t C, const float *x, float *out, int32_t accumulate, void *stream);
+/* Relative L2 of pred against tgt ([B][npix][CH], CH <= 8): stats[(b CH + c)
+ * 2 + {0, 1}] = (|pred - tgt|^2, |tgt|^2) per sample and channel; with dpred
+ * also the gradient of the mean over (b, c) of their ratio.             */
+sg_status sg_nn_rel_l2(int32_t B, int64_t npix, int32_t CH, const float *pred, const float *tgt, float *stats,
+                       float *dpred, void *stream);
+/* Adam step (bias-corrected for `step` >= 1) on float weights w with
+ * moments m, v; also refreshes the bf16 copy w_bf16 when non-NULL.       */
+sg_status sg_nn_adam(int64_t n, float *w, const float *g, float *m, float *v, float lr, float b1, float b2, float eps,
+                     int32_t step, void *w_bf16, void *stream);
+/* float -> bf16 copy; transpose of a float [rows][cols] matrix to bf16
+ * [cols][rows].                                                          */
+sg_status sg_nn_cast(int64_t n, const float *x, void *y_bf16, void *stream);
+sg_status sg_nn_transpose(int32_t rows, int32_t cols, const float *x, void *y_bf16, void *stream);
+/* Seeded training fields on an nr x nphi log-polar grid for B samples from
+ * per-sample parameters (float [B][NPAR], layout in surrogate.py): gas
+ * Sigma_g (log-normal-like background, m = 1..6 spirals, Gaussian clumps) and,
+ * when sigma_d is non-NULL, dust as a noisy fraction of it; [B][nr][nphi]. */
+sg_status sg_nn_fields(int32_t B, int32_t nr, int32_t nphi, const float *params, float *sigma_g, float *sigma_d,
+                       void *stream);
+
+/* Network input x [B][nr][nphi][7] (bf16) = (Sigma_g s_g, Sigma_d s_d, h_g / 0.05,
+ * h_d / 0.05, (i + 1/2) / nr, cos phi_j, sin phi_j) with per_sample [B][4]
+ * = (s_g, s_d, h_g, h_d); sigma_d may be NULL (channel 1 = 0).  Targets:
+ * t [B][npix][2] = (a, c) scale[b]; with unpack the inverse (a, c written). */
+sg_status sg_nn_pack_inputs(int32_t B, int32_t nr, int32_t nphi, const float *sigma_g, const float *sigma_d,
+                            const float *per_sample, void *x_bf16, void *stream);
+sg_status sg_nn_pack_targets(int32_t B, int64_t npix, const float *a, const float *c, const float *scale, float *t,
+                             int32_t unpack, void *stream);
+
 /* Release a plan and all its device memory (NULL is a no-op).  Synchronises
  * the device before freeing.                                               */
 void sg_destroy(sg_plan *plan);

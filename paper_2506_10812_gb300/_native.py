@@ -27,7 +27,9 @@ ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf1
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
            "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_set_column_engine", "sg_batch_create", "sg_batch_solve",
            "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_tune_results", "sg_batch_destroy",
-           "sg_batch_last_error", "sg_destroy", "sg_status_string", "sg_last_error")
+           "sg_batch_last_error", "sg_nn_gemm", "sg_nn_spec_combine", "sg_nn_spec_combine_bwd", "sg_nn_modemix",
+           "sg_nn_modemix_bwd", "sg_nn_act", "sg_nn_act_bwd", "sg_nn_colsum", "sg_nn_rel_l2", "sg_nn_adam", "sg_nn_cast",
+           "sg_nn_transpose", "sg_nn_fields", "sg_nn_pack_inputs", "sg_nn_pack_targets", "sg_destroy", "sg_status_string", "sg_last_error")
 
 
 class SgParams(ctypes.Structure):
@@ -105,6 +107,27 @@ def load() -> ctypes.CDLL:
     lib.sg_batch_last_error.restype = ctypes.c_char_p
     lib.sg_set_column_engine.argtypes = [vp, i32]
     lib.sg_set_column_engine.restype = st
+    i64, f32 = ctypes.c_int64, ctypes.c_float
+    nn = {
+        "sg_nn_gemm": [i32, i32, i32, i32, f32, vp, i32, i64, i32, vp, i32, i64, f32, vp, i32, i64, vp, vp, vp],
+        "sg_nn_spec_combine": [i32, i32, i32, i32, vp, vp, vp],
+        "sg_nn_spec_combine_bwd": [i32, i32, i32, i32, vp, vp, vp],
+        "sg_nn_modemix": [i32, i32, i32, i32, vp, vp, vp, vp],
+        "sg_nn_modemix_bwd": [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp],
+        "sg_nn_act": [i64, vp, vp, i32, vp],
+        "sg_nn_act_bwd": [i64, vp, vp, vp, vp, i32, vp],
+        "sg_nn_colsum": [i64, i32, vp, vp, i32, vp],
+        "sg_nn_rel_l2": [i32, i64, i32, vp, vp, vp, vp, vp],
+        "sg_nn_adam": [i64, vp, vp, vp, vp, f32, f32, f32, f32, i32, vp, vp],
+        "sg_nn_cast": [i64, vp, vp, vp],
+        "sg_nn_transpose": [i32, i32, vp, vp, vp],
+        "sg_nn_fields": [i32, i32, i32, vp, vp, vp, vp],
+        "sg_nn_pack_inputs": [i32, i32, i32, vp, vp, vp, vp, vp],
+        "sg_nn_pack_targets": [i32, i64, vp, vp, vp, vp, i32, vp],
+    }
+    for name, args in nn.items():
+        getattr(lib, name).argtypes = args
+        getattr(lib, name).restype = st
     lib.sg_launches_per_solve.argtypes = [vp, u32]
     lib.sg_launches_per_solve.restype = i32
     lib.sg_destroy.argtypes = [vp]

@@ -22,7 +22,7 @@ def lib():
 def declared_functions():
     txt = open(os.path.join(ROOT, "include", "sg.h")).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(sg_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(sg_[a-z0-9_]+)\s*\(", txt)))
 
 
 def test_header_declares_the_five_paper_entry_points():

@@ -1,0 +1,141 @@
+"""GPU tests of the neural-operator surrogate kernels and model: the BF16
+tensor-core GEMM against float64 products of the same BF16 values; the whole
+network's forward output and every parameter gradient against a float64
+CPU reference (plain torch ops with autograd, same weights, same DFT
+matrices) on a tiny grid; a short training run lowers the loss; the gate
+falls back to the exact path bit for bit."""
+import math
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+from paper_2506_10812_gb300 import _native as N
+from paper_2506_10812_gb300 import build as B
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    B.build()
+    N.load()
+
+
+def bf(t):
+    return t.to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("batch,M,Nn,K,trans_a,alpha,beta,bias", [
+    (1, 64, 64, 32, False, 1.0, 0.0, False), (3, 100, 70, 45, False, 0.5, 1.0, True),
+    (2, 33, 130, 200, True, 1.0, 0.0, False), (5, 7, 2, 4096, True, 1.0, 0.5, True),
+    (1, 1000, 32, 7, False, 1.0, 0.0, True)])
+def test_gemm(batch, M, Nn, K, trans_a, alpha, beta, bias):
+    dev = torch.device("cuda:0")
+    g = torch.Generator().manual_seed(M * 7 + K)
+    A = torch.randn(batch, K, M, generator=g) if trans_a else torch.randn(batch, M, K, generator=g)
+    Bm = torch.randn(batch, K, Nn, generator=g)
+    C0 = torch.randn(batch, M, Nn, generator=g)
+    bv = torch.randn(Nn, generator=g)
+    Ad, Bd = bf(A).to(dev), bf(Bm).to(dev)
+    Cd = C0.to(dev).contiguous()
+    Cb = torch.empty(batch, M, Nn, dtype=torch.bfloat16, device=dev)
+    lib = N.load()
+    vp = lambda t: t.data_ptr() if t is not None else None
+    st = lib.sg_nn_gemm(batch, M, Nn, K, alpha, vp(Ad), M if trans_a else K, Ad[0].numel(), int(trans_a), vp(Bd),
+                        Nn, Bd[0].numel(), beta, vp(Cd), Nn, M * Nn, vp(Cb),
+                        vp(bv.to(dev)) if bias else None, None)
+    assert st == 0
+    torch.cuda.synchronize()
+    Af = bf(A).double()
+    opA = Af.transpose(1, 2) if trans_a else Af
+    ref = alpha * opA @ bf(Bm).double() + beta * C0.double() + (bv.double() if bias else 0.0)
+    got = Cd.double().cpu()
+    assert (got - ref).abs().max() <= 1e-5 * ref.abs().max() * math.sqrt(K) + 1e-6
+    assert torch.allclose(Cb.double().cpu(), got, rtol=1e-2, atol=1e-2 * ref.abs().max())
+
+
+# ---------------------------------------------------------------- network
+def reference_loss(S):
+    """The surrogate's forward pass and loss in float64 on the CPU (torch
+    ops, autograd), from the model's own weights and DFT matrices."""
+    Bn, R, P, C, M1, K1 = S.B, S.nr, S.nphi, 32, 16, 32
+    n = Bn * R * P
+    d = lambda t: t.detach().double().cpu()
+    leaf = {}
+
+    def w(name, use_bf16):
+        src = S.P[name]["b"] if use_bf16 else S.P[name]["w"]
+        t = d(src).clone().requires_grad_(True)
+        leaf[name] = t
+        return t
+
+    x = d(S.x)
+    tgt = d(S.tgt)
+    Fphi, Gr, Hr, Hre, Him = d(S.Fphi), d(S.Gr), d(S.Hr), d(S.Hre), d(S.Him)
+    v = x @ w("Pw", True) + w("Pb", False)
+    for l in range(4):
+        vi = v.reshape(Bn, R, P, C)
+        V1 = torch.einsum("jp,brpc->brjc", Fphi, vi)
+        T = torch.einsum("kr,brjc->bkjc", Gr, V1)
+        Tc, Ts = T[:, :K1], T[:, K1:]
+        V2r = Tc[:, :, 0::2] - Ts[:, :, 1::2]
+        V2i = Tc[:, :, 1::2] + Ts[:, :, 0::2]
+        Sw = w(f"S{l}", False)
+        Wr, Wi = Sw[..., 0], Sw[..., 1]
+        Or = torch.einsum("bkmi,kmio->bkmo", V2r, Wr) - torch.einsum("bkmi,kmio->bkmo", V2i, Wi)
+        Oi = torch.einsum("bkmi,kmio->bkmo", V2r, Wi) + torch.einsum("bkmi,kmio->bkmo", V2i, Wr)
+        U1 = torch.einsum("rk,bkmc->brmc", Hr, torch.cat([Or, Oi], dim=1))
+        u = torch.einsum("pm,brmc->brpc", Hre, U1[:, :R]) + torch.einsum("pm,brmc->brpc", Him, U1[:, R:])
+        pre = u.reshape(n, C) + v @ w(f"W{l}", True) + w(f"b{l}", False)
+        v = F.gelu(pre) if l < 3 else pre
+    q = F.gelu(v @ w("Q1", True) + w("q1", False))
+    out = q @ w("Q2", True) + w("q2", False)
+    o, t = out.reshape(Bn, -1, 2), tgt.reshape(Bn, -1, 2)
+    loss = (((o - t) ** 2).sum(1) / (t ** 2).sum(1)).mean()
+    loss.backward()
+    return out.detach(), loss.detach(), {k: v.grad for k, v in leaf.items()}
+
+
+def rel(a, b):
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def test_forward_and_gradients_match_reference():
+    from paper_2506_10812_gb300.surrogate import Surrogate
+    S = Surrogate(nr=32, nphi=64, batch=2, seed=3)
+    S.load([11, 12])
+    S.forward()
+    L, _ = S.loss(grad=True)
+    S.backward()
+    torch.cuda.synchronize()
+    out, Lref, grads = reference_loss(S)
+    assert rel(S.out.double().cpu(), out) < 3e-2
+    assert abs(L - float(Lref)) < 3e-2 * float(Lref)
+    for name, g in grads.items():
+        got = S.P[name]["g"].double().cpu().reshape(g.shape)
+        assert rel(got, g) < 1e-1, (name, rel(got, g))
+
+
+def test_training_lowers_the_loss_and_gate():
+    from paper_2506_10812_gb300 import Plan
+    from paper_2506_10812_gb300.surrogate import GATE, Surrogate
+    S = Surrogate(nr=32, nphi=64, batch=2, seed=5)
+    hist = S.train(60, lr=3e-3, seed0=100)
+    assert np.mean(hist[-10:]) < 0.5 * np.mean(hist[:5])
+    rel_val = S.validate([900, 901, 902, 903])
+    assert S.val_error == pytest.approx(float(np.max(rel_val)))
+    # above the gate: the exact path, bit for bit
+    S.val_error = 10 * GATE
+    S.load([77, 78])
+    h_g, St = 0.05, 0.1
+    gr, gphi, used = S.solve(S.sg[0].clone(), S.sd[0].clone(), h_g, St)
+    assert not used
+    p = S._plan(h_g, St)
+    ref = p.solve(S.sg[0].clone(), S.sd[0].clone(), outputs=("gr", "gphi"))
+    assert torch.equal(gr, ref["gr_g"]) and torch.equal(gphi, ref["gphi_g"])
+    # within the gate: the network's fields
+    S.val_error = 0.0
+    gr2, gphi2, used2 = S.solve(S.sg[0].clone(), S.sd[0].clone(), h_g, St)
+    assert used2 and torch.isfinite(gr2).all() and not torch.equal(gr2, gr)
