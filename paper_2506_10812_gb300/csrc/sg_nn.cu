@@ -34,7 +34,7 @@ template <bool TA>
 __global__ void __launch_bounds__(128)
 k_gemm(int M, int N, int K, float alpha, const __nv_bfloat16 *__restrict__ A, int lda, long long sa,
        const __nv_bfloat16 *__restrict__ B, int ldb, long long sb, float beta, float *__restrict__ C, int ldc,
-       long long sc, __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ bias)
+       long long sc, __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ bias, int vecA, int vecB)
 {
     __shared__ __align__(16) __nv_bfloat16 As[BM][SK];
     __shared__ __align__(16) __nv_bfloat16 Bs[BN][SK];
@@ -48,26 +48,75 @@ k_gemm(int M, int N, int K, float alpha, const __nv_bfloat16 *__restrict__ A, in
     float acc[2][4][4] = {};
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
     for (int k0 = 0; k0 < K; k0 += BK) {
-        // A tile: BM x BK
-        for (int i = tid; i < BM * BK; i += 128) {
-            int m, k;
-            if (TA) {                   // A stored [K][M]: m fastest for coalescing
-                m = i % BM;
-                k = i / BM;
-            } else {
-                k = i % BK;
-                m = i / BK;
+        // A tile: BM x BK.  vecA: 8 consecutive elements along the stored
+        // row (k for A, m for A^T) per 16-byte load where fully in range.
+        if (vecA) {
+            for (int i = tid; i < BM * BK / 8; i += 128) {
+                int m, k;
+                if (TA) {
+                    m = (i % (BM / 8)) * 8;
+                    k = i / (BM / 8);
+                } else {
+                    k = (i % (BK / 8)) * 8;
+                    m = i / (BK / 8);
+                }
+                const int gm = m0 + m, gk = k0 + k;
+                if (TA) {
+                    if (gk < K && gm + 8 <= M) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(A + (size_t)gk * lda + gm);
+                        const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) As[m + j][k] = e[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) As[m + j][k] = (gk < K && gm + j < M) ? A[(size_t)gk * lda + gm + j] : zero;
+                    }
+                } else {
+                    if (gm < M && gk + 8 <= K) {
+                        *reinterpret_cast<uint4 *>(&As[m][k]) = *reinterpret_cast<const uint4 *>(A + (size_t)gm * lda + gk);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) As[m][k + j] = (gm < M && gk + j < K) ? A[(size_t)gm * lda + gk + j] : zero;
+                    }
+                }
             }
-            const int gm = m0 + m, gk = k0 + k;
-            __nv_bfloat16 v = zero;
-            if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-            As[m][k] = v;
+        } else {
+            for (int i = tid; i < BM * BK; i += 128) {
+                int m, k;
+                if (TA) {                   // A stored [K][M]: m fastest for coalescing
+                    m = i % BM;
+                    k = i / BM;
+                } else {
+                    k = i % BK;
+                    m = i / BK;
+                }
+                const int gm = m0 + m, gk = k0 + k;
+                __nv_bfloat16 v = zero;
+                if (gm < M && gk < K) v = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+                As[m][k] = v;
+            }
         }
         // B tile: BK x BN stored [n][k]
-        for (int i = tid; i < BK * BN; i += 128) {
-            const int n = i % BN, k = i / BN;
-            const int gn = n0 + n, gk = k0 + k;
-            Bs[n][k] = (gn < N && gk < K) ? B[(size_t)gk * ldb + gn] : zero;
+        if (vecB) {
+            for (int i = tid; i < BK * BN / 8; i += 128) {
+                const int n = (i % (BN / 8)) * 8, k = i / (BN / 8);
+                const int gn = n0 + n, gk = k0 + k;
+                if (gk < K && gn + 8 <= N) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(B + (size_t)gk * ldb + gn);
+                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) Bs[n + j][k] = e[j];
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) Bs[n + j][k] = (gk < K && gn + j < N) ? B[(size_t)gk * ldb + gn + j] : zero;
+                }
+            }
+        } else {
+            for (int i = tid; i < BK * BN; i += 128) {
+                const int n = i % BN, k = i / BN;
+                const int gn = n0 + n, gk = k0 + k;
+                Bs[n][k] = (gn < N && gk < K) ? B[(size_t)gk * ldb + gn] : zero;
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -132,12 +181,15 @@ extern "C" sg_status sg_nn_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, 
     cudaStream_t s = (cudaStream_t)stream;
     auto a = (const __nv_bfloat16 *)A;
     auto b = (const __nv_bfloat16 *)B;
+    // 16-byte loads need 16-byte aligned rows in every batch entry
+    const int vecA = (lda % 8 == 0) && (stride_a % 8 == 0) && ((uintptr_t)A % 16 == 0);
+    const int vecB = (ldb % 8 == 0) && (stride_b % 8 == 0) && ((uintptr_t)B % 16 == 0);
     if (trans_a)
         k_gemm<true><<<grid, 128, 0, s>>>(M, N, K, alpha, a, lda, stride_a, b, ldb, stride_b, beta, C, ldc, stride_c,
-                                          (__nv_bfloat16 *)C_bf16, bias);
+                                          (__nv_bfloat16 *)C_bf16, bias, vecA, vecB);
     else
         k_gemm<false><<<grid, 128, 0, s>>>(M, N, K, alpha, a, lda, stride_a, b, ldb, stride_b, beta, C, ldc, stride_c,
-                                           (__nv_bfloat16 *)C_bf16, bias);
+                                           (__nv_bfloat16 *)C_bf16, bias, vecA, vecB);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
@@ -260,20 +312,22 @@ __global__ void k_act_bwd(long long n, const float *__restrict__ pre, const floa
     }
 }
 
-// out[c] (+)= sum over rows of x[rows][C]
-__global__ void k_colsum(long long rows, int C, const float *__restrict__ x, float *__restrict__ out, int accumulate)
+// out[c] += sum over a chunk of rows of x[rows][C] (blockIdx.y: row chunk);
+// out is zeroed (or kept) by the caller before the launch.
+__global__ void k_colsum(long long rows, int C, long long chunk, const float *__restrict__ x, float *__restrict__ out)
 {
     __shared__ float red[256];
     const int c = blockIdx.x;
+    const long long r0 = blockIdx.y * chunk, r1 = r0 + chunk < rows ? r0 + chunk : rows;
     float s = 0.f;
-    for (long long r = threadIdx.x; r < rows; r += blockDim.x) s += x[r * C + c];
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) s += x[r * C + c];
     red[threadIdx.x] = s;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[c] = (accumulate ? out[c] : 0.f) + red[0];
+    if (threadIdx.x == 0) atomicAdd(&out[c], red[0]);
 }
 
 // Relative-L2 loss per (sample, channel): pred, target [B][npix][2];
@@ -412,7 +466,15 @@ sg_status sg_nn_act_bwd(int64_t n, const float *pre, const float *dy, float *dpr
 sg_status sg_nn_colsum(int64_t rows, int32_t C, const float *x, float *out, int32_t accumulate, void *stream)
 {
     if (!x || !out || rows < 1 || C < 1) return SG_ERR_ARG;
-    k_colsum<<<C, 256, 0, (cudaStream_t)stream>>>(rows, C, x, out, accumulate);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!accumulate) cudaMemsetAsync(out, 0, sizeof(float) * C, s);
+    // enough row chunks to fill the GPU (about 2048 blocks), at least 4096 rows each
+    long long chunks = 2048 / C + 1;
+    if (rows / chunks < 4096) chunks = rows / 4096 + 1;
+    if (chunks > 65535) chunks = 65535;
+    const long long chunk = (rows + chunks - 1) / chunks;
+    dim3 grid(C, (unsigned)chunks);
+    k_colsum<<<grid, 256, 0, s>>>(rows, C, chunk, x, out);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 

@@ -30,7 +30,10 @@ def bf(t):
 @pytest.mark.parametrize("batch,M,Nn,K,trans_a,alpha,beta,bias", [
     (1, 64, 64, 32, False, 1.0, 0.0, False), (3, 100, 70, 45, False, 0.5, 1.0, True),
     (2, 33, 130, 200, True, 1.0, 0.0, False), (5, 7, 2, 4096, True, 1.0, 0.5, True),
-    (1, 1000, 32, 7, False, 1.0, 0.0, True)])
+    (1, 1000, 32, 7, False, 1.0, 0.0, True),
+    # 16-byte load paths (leading dimensions multiples of 8) with ragged tiles
+    (2, 72, 40, 96, True, 1.0, 0.0, True), (1, 130, 24, 40, False, 2.0, 0.0, False),
+    (4, 64, 64, 64, False, 1.0, 1.0, True)])
 def test_gemm(batch, M, Nn, K, trans_a, alpha, beta, bias):
     dev = torch.device("cuda:0")
     g = torch.Generator().manual_seed(M * 7 + K)
