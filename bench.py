@@ -320,7 +320,9 @@ def run_ours(args):
                 "traffic": profiled_traffic() if args.engine == "fft32" else None,
                 "peak_source": f"{peak_kind} HBM copy bandwidth", "algorithmic_bytes_per_launch": col_bytes}
     # whole step against the 3-pass model traffic (60 B/cell gas-only with Phi)
-    step_bytes = col_bytes + 8 * nsrc * N * nr * 2 + 4 * nsrc * d.cells + 8 * nsrc * ncomp * N * nr + 4 * nsrc * ncomp * d.cells
+    # col_bytes holds the spectra read, the kernel spectra and the column output written; add the inputs,
+    # the row spectra written, the column output read back and the outputs written
+    step_bytes = col_bytes + 8 * nsrc * N * nr + 4 * nsrc * d.cells + 8 * nsrc * ncomp * N * nr + 4 * nsrc * ncomp * d.cells
     step_frac = step_bytes / (ms_per_step * 1e-3) / 1e9 / peak
 
     # ---- end to end through the C ABI with host buffers (pinned)

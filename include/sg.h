@@ -130,7 +130,11 @@ sg_status sg_accel(sg_plan *plan, const void *sigma_g, const void *sigma_d,
                    void *gr_g, void *gphi_g, void *gr_d, void *gphi_d, void *stream);
 
 /* sg_potential and sg_accel fused: one forward transform of each source
- * serves every requested output.  Any output pointer may be NULL.          */
+ * serves every requested output.  Any output pointer may be NULL.
+ * For these three entry points every input and output is a device buffer
+ * of nr * nphi elements of the plan dtype, aligned to two elements (8 bytes
+ * for SG_F32, 16 for SG_F64; any cudaMalloc or torch allocation is); a
+ * misaligned buffer is rejected with SG_ERR_ARG.                           */
 sg_status sg_solve(sg_plan *plan, const void *sigma_g, const void *sigma_d,
                    void *phi_g, void *gr_g, void *gphi_g,
                    void *phi_d, void *gr_d, void *gphi_d, void *stream);

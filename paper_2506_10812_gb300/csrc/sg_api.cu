@@ -227,7 +227,8 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
     if (ev) cudaEventRecord(pl->ev[0], s);
     if (pl->p.method == SG_METHOD_FFT) {
         e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row,
-                               pl->twp_row, (const R *)pl->rcen, true, s);
+                               pl->twp_row, (const R *)pl->rcen, true, s, 0, -1, pl->tm_rows ? &pl->tm_sh : nullptr,
+                               pl->flag);
         if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
         if (ev) cudaEventRecord(pl->ev[1], s);
         e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
@@ -243,7 +244,8 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
             ro.is_phi[ro.n] = (q % 3) == SG_COMP_PHI;
             ++ro.n;
         }
-        e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s);
+        e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, 0, -1,
+                               pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag);
         if (e != cudaSuccess) return cuda_fail(pl, e, "inverse row transform");
         if (ev) cudaEventRecord(pl->ev[3], s);
     } else {
@@ -269,6 +271,11 @@ sg_status solve_any(sg_plan *pl, const void *sg_, const void *sd_, void *const o
     if (st != SG_OK) return st;
     if (!sg_) return fail(pl, SG_ERR_ARG, "sigma_g is NULL");
     if (pl->nsrc == 2 && !sd_) return fail(pl, SG_ERR_ARG, "bi-fluid plan needs sigma_d");
+    // the row transforms move element pairs
+    const uintptr_t amask = 2 * pl->esz - 1;
+    bool misaligned = ((uintptr_t)sg_ & amask) || (pl->nsrc == 2 && ((uintptr_t)sd_ & amask));
+    for (int q = 0; q < 6; ++q) misaligned |= ((uintptr_t)outs[q] & amask) != 0;
+    if (misaligned) return fail(pl, SG_ERR_ARG, "device buffers must be aligned to %d bytes", (int)(amask + 1));
     cudaStream_t s = (cudaStream_t)stream;
     return pl->f64 ? solve_t<double>(pl, sg_, sd_, outs, s) : solve_t<float>(pl, sg_, sd_, outs, s);
 }
@@ -304,7 +311,7 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ein[k], 0);
         if (e == cudaSuccess)
             e = launch_rows_fwd<R>(dsg, dsd, pl->nsrc, pl->sh, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen,
-                                   true, s, k * rows, rows);
+                                   true, s, k * rows, rows, pl->tm_rows ? &pl->tm_sh : nullptr, pl->flag);
     }
     if (e != cudaSuccess) return cuda_fail(pl, e, "pipelined input and row transform");
     if (!mask) return cuda_fail(pl, cudaStreamSynchronize(s), "solve");
@@ -322,7 +329,7 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     }
     for (int k = 0; k < nch && e == cudaSuccess; ++k) {
         e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, k * rows,
-                               rows);
+                               rows, pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag);
         if (e == cudaSuccess) e = cudaEventRecord(eout[k], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c, eout[k], 0);
         const size_t off = (size_t)k * rows * row_b, len = (size_t)rows * row_b;
@@ -434,6 +441,9 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
                "kernel spectra");
         SG_TRY(cudaMalloc(&pl->sh, (size_t)pl->nsrc * pl->N * p->nr * cbytes), "scratch");
         SG_TRY(cudaMalloc(&pl->oh, (size_t)pl->nsrc * 3 * pl->N * p->nr * cbytes), "scratch");
+        if (rows_tma_eligible(p->nr, p->nphi, pl->f64))
+            pl->tm_rows = encode_row_map(&pl->tm_sh, pl->sh, p->nr, (long long)pl->nsrc * pl->N) == cudaSuccess &&
+                          encode_row_map(&pl->tm_oh, pl->oh, p->nr, (long long)pl->nsrc * 3 * pl->N) == cudaSuccess;
         sg_status st = build_tables(pl, s);
         if (st != SG_OK) {
             fprintf(stderr, "sg_plan_create: %s\n", pl->err);
@@ -587,7 +597,7 @@ sg_status sg_sync(sg_plan *pl, void *stream)
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->flag, 0, sizeof(unsigned int), s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(pl, e, "sg_sync");
-    if (h & 2u) return fail(pl, SG_ERR_TIMEOUT, "a staged kernel-spectrum copy did not complete");
+    if (h & 2u) return fail(pl, SG_ERR_TIMEOUT, "a staged bulk copy did not complete");
     if (h & 1u) return fail(pl, SG_ERR_NONFINITE, "non-finite value in an output");
     return SG_OK;
 }

@@ -2,6 +2,7 @@
 // (sg_kernels.cu, sg_direct.cu).  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -40,10 +41,20 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 // (slot m = 0 packs the real m = 0 and m = nphi/2 coefficients).
 // row0, nrows_run: transform only rows row0 .. row0 + nrows_run - 1 (multiples
 // of row_rpc; nrows_run < 0: to the end); nrows stays the row stride.
+// tm: the tensor map of xh (encode_row_map over nsrc nphi/2 columns); with
+// it, FP32 rows of the hot lengths (rows_tma_eligible) store their spectrum
+// tiles by bulk tensor copies (bit 2 of *tflag when a staged copy never
+// completed).
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
                             const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s,
-                            int row0 = 0, int nrows_run = -1);
+                            int row0 = 0, int nrows_run = -1, const CUtensorMap *tm = nullptr,
+                            unsigned int *tflag = nullptr);
+
+// 2-D tensor map of a [ncols][nr] complex FP32 intermediate for the
+// tensor-copy row transforms; rows_tma_eligible: the sizes they take.
+cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols);
+bool rows_tma_eligible(int nr, int nphi, bool f64);
 
 // Column pass of the solve: forward padded FFT of every source column,
 // products with the packed kernel spectra, inverse FFT of every requested
@@ -80,10 +91,13 @@ struct RowOut {
 // Inverse row transforms (C2R) of the column-pass output and the epilogue
 // (accelerations divided by r_i, undoing the radial source scaling; finite
 // check into *flag bit 1 when flag != NULL).
+// tm: the tensor map of oh (all nsrc * 3 spectra); with it, FP32 rows of the
+// hot lengths load their tiles by bulk tensor copies (bit 2 of *tflag when a
+// copy never completed).
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
                             const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s, int row0 = 0,
-                            int nrows_run = -1);
+                            int nrows_run = -1, const CUtensorMap *tm = nullptr, unsigned int *tflag = nullptr);
 
 // Indirect term (App. E): out[2 a + {0, 1}] = (A_a, B_a) in FP64; partial
 // holds indirect_blocks(nphi) x 4 doubles.
@@ -125,5 +139,7 @@ struct sg_plan {
     cudaStream_t cstream = nullptr;       // sg_solve_host: copy stream of the pipelined solve
     cudaEvent_t cev[2 * 16] = {};         // sg_solve_host: per-chunk copy / compute events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events
+    bool tm_rows = false;                 // tensor maps below are valid (rows_tma_eligible)
+    CUtensorMap tm_sh{}, tm_oh{};         // the row transforms' views of sh and oh
     char err[256] = {0};
 };

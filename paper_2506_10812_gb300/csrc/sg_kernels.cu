@@ -40,6 +40,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <type_traits>
+
 #include "sg_bessel.cuh"
 #include "sg_fft.cuh"
 #include "sg_internal.h"
@@ -148,6 +151,163 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
     k_tab_eval<<<blocks, 256, 0, s>>>(nr, nphi, du, ha, hb, scale, alpha, mixed ? 1 : 0, o64[0], o64[1],
                                       o64[2], o32[0], o32[1], o32[2]);
     return cudaGetLastError();
+}
+
+// ------------------------------------------- tensor-copy row transforms
+// FP32 row transforms of the hot lengths (nphi = 2 NC, NC = 1024 or 2048),
+// four rows per CTA, whose [N][rows] side moves by 2-D tensor copies: the
+// forward transform leaves its [N][4] spectrum tile with bulk tensor stores,
+// the inverse transform receives its tile by bulk tensor loads, so neither
+// spends load/store-unit instructions on the 32-byte column slices.  The
+// tile is dense, (k, g) at 4 k + g; lane l of warp w owns row g = l & 3 and
+// transform thread t = 8 w + (l >> 2), so each half-warp (the unit in which
+// shared memory serves 8-byte accesses) touches 16 consecutive tile slots.
+// Row g's exchange buffer starts at g * row_pitch_tma(N) elements, a pitch
+// = 4 (mod 16): a half-warp's 4 rows x 4 consecutive indices then fall in 16
+// distinct bank pairs in every transform exchange.
+// The forward kernel also stages its four input rows by 1-D bulk copies (so
+// it needs 16-byte aligned inputs; the launch falls back to the transpose
+// kernel otherwise).  On the 2048 x 4096 disc the pair takes 28.0 + 52.5 us
+// per solve against 30.5 + 64.0 us for the load/store-unit transpose
+// kernels; computing tw(t + T e) from tw(t) measured faster than loading it.
+#ifndef SG_ROWS_FWD_TMA
+#define SG_ROWS_FWD_TMA 1          // 0: forward rows by the load/store-unit transpose kernel
+#endif
+constexpr int kRowHdr = 1024;                     // mbarrier + partial sums; the tile starts 1024-aligned
+__host__ __device__ constexpr int row_pitch_tma(int N) { return padded_len(N) + 3; }
+size_t row_tma_smem_bytes(int N)
+{
+    const size_t tile = (size_t)N * 4 * 8, xb = (size_t)4 * row_pitch_tma(N) * 8;
+    return kRowHdr + (tile > xb ? tile : xb);
+}
+
+// cos(2 pi e / 32), e = 0..8
+__device__ constexpr double kCos32[9] = {1.0,
+                                         0.98078528040323044913,
+                                         0.92387953251128675613,
+                                         0.83146961230254523708,
+                                         0.70710678118654752440,
+                                         0.55557023301960222474,
+                                         0.38268343236508977173,
+                                         0.19509032201612826785,
+                                         0.0};
+// exp(-2 pi i e / 32), e = 0..15
+template <int E> __device__ __forceinline__ float2 root32()
+{
+    constexpr double c = E <= 8 ? kCos32[E] : -kCos32[16 - E];
+    constexpr double s = E <= 8 ? kCos32[8 - E] : kCos32[E - 8];
+    return make_float2((float)c, (float)-s);
+}
+// tw(t + T e) = exp(-2 pi i (t + T e) / nphi) with T / nphi = 1 / 32: the
+// loaded tw(t) times a compile-time root (one extra rounding)
+template <int E> __device__ __forceinline__ float2 tw_step(float2 w0)
+{
+    if constexpr (E == 0) return w0;
+    else return cmul(w0, root32<E>());
+}
+template <int E, typename F> __device__ __forceinline__ void unroll16(F &&f)
+{
+    if constexpr (E < 16) {
+        f(std::integral_constant<int, E>{});
+        unroll16<E + 1>(f);
+    }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(NC / 4, 4096 / NC)
+k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const __grid_constant__ CUtensorMap tm,
+               const float2 *__restrict__ tw, const float2 *__restrict__ twp, const float *__restrict__ rscale,
+               int dc, unsigned int *tflag, int row0)
+{
+    constexpr int N = NC, T = N / 16, NW = T / 8, PLS = row_pitch_tma(N), XS = T + T / 16;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float *red = reinterpret_cast<float *>(smem_raw + 64);              // NW x 4 partial sums
+    float2 *reg = reinterpret_cast<float2 *>(smem_raw + kRowHdr);
+    if (smem_u32(reg) & 127u) {                                         // TMA alignment (never expected)
+        if (threadIdx.x == 0 && tflag) atomicOr(tflag, 2u);
+        return;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane & 3, t = (w << 3) | (lane >> 2);
+    const int a = blockIdx.y, i0 = row0 + blockIdx.x * 4, i = i0 + g;
+    const float *xa = a == 0 ? x0 : x1;
+    const float sc = rscale ? rscale[i] : 1.f;
+    float2 v[16];
+    {
+        // the four rows (contiguous) land at a pitch of N + 4 complex, which
+        // keeps the 4-row x 4-column half-warp reads conflict-free; the
+        // staging overlays the exchange buffers (the transform synchronises first)
+        constexpr int IPS = N + 4;
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+        if (threadIdx.x == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint64_t pf = l2_evict_first();
+            mbar_expect_tx(bar, (unsigned)N * 32u);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) tma_load_1d(reg + r * IPS, xa + (size_t)(i0 + r) * 2 * N, N * 8, bar, pf);
+        }
+        if (!__syncthreads_and(mbar_wait_bounded(bar, 0, tflag))) return;
+        const float2 *xs = reg + g * IPS + t;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {                    // z[n] = x[2n] + i x[2n+1]
+            const float2 z = xs[T * e];
+            v[e] = make_float2(z.x * sc, z.y * sc);
+        }
+    }
+    float mean = 0.f;
+    if (dc) {
+        float s = 0.f;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) s += v[e].x + v[e].y;
+        // lanes of one row differ in bits 2..4
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 8);
+        s += __shfl_xor_sync(0xffffffffu, s, 16);
+        if (lane < 4) red[w * 4 + lane] = s;
+        __syncthreads();
+        s = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) s += red[ww * 4 + g];
+        mean = s / (float)(2 * N);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = make_float2(v[e].x - mean, v[e].y - mean);
+    }
+    float2 *xb = reg + g * PLS;
+    fft_ct<true, N>(v, t, xb, twp);
+    // X[k] = E[k] + W^k O[k], E = (Z[k] + Z*[N-k]) / 2, O = (Z[k] - Z*[N-k]) / 2i
+    __syncthreads();
+    float2 *zs = xb + t + (t >> 4);                       // pidx(t + T e) = t + (t >> 4) + e XS
+#pragma unroll
+    for (int e = 0; e < 16; ++e) zs[e * XS] = v[e];
+    __syncthreads();
+    const float2 *zc = xb + (N - t) + (N >> 4) + ((-t) >> 4);   // pidx(N - k) = zc - e XS
+    const float2 w0 = __ldg(&tw[t]);
+    unroll16<0>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        const float2 Z = v[e];
+        if (e == 0 && t == 0) {
+            // (X[0], X[nphi/2]) packed; the mean only enters X[0]
+            v[e] = make_float2(Z.x + Z.y + mean * (float)(2 * N), Z.x - Z.y);
+        } else {
+            const float2 Zc = cconj(zc[-e * XS]);
+            const float2 E = cscale(cadd(Z, Zc), 0.5f);
+            const float2 O = cscale(cmul_mi(csub(Z, Zc)), 0.5f);
+            v[e] = cadd(E, cmul(O, tw_step<e>(w0)));
+        }
+    });
+    __syncthreads();                                      // the tile overwrites the exchange buffers
+    float2 *tl = reg + 4 * t + g;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) tl[4 * T * e] = v[e];
+    fence_proxy_async();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t pl = l2_evict_last();
+#pragma unroll
+        for (int b = 0; b < N / 256; ++b) tma_store_2d(&tm, 2 * i0, a * N + 256 * b, reg + 4 * 256 * b, pl);
+        bulk_commit();
+        bulk_wait_read_all();
+    }
 }
 
 // ------------------------------------------------------------ row R2C
@@ -259,12 +419,25 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
                             const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s,
-                            int row0, int nrows_run)
+                            int row0, int nrows_run, const CUtensorMap *tm, unsigned int *tflag)
 {
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
     if (nrows_run < 0) nrows_run = nrows - row0;
     dim3 grid(nrows_run / rpc, nsrc);
+    if constexpr (sizeof(R) == 4 && SG_ROWS_FWD_TMA) {
+        const bool aligned = ((uintptr_t)x0 & 15u) == 0 && ((uintptr_t)x1 & 15u) == 0;
+        if (tm && aligned && rows_tma_eligible(nrows, nphi, false)) {
+            auto go = [&](auto kern, int N) {
+                kern<<<grid, N / 4, row_tma_smem_bytes(N), s>>>(x0, x1, *tm, (const float2 *)tw_row,
+                                                               (const float2 *)twp_row, rscale, dc ? 1 : 0, tflag,
+                                                               row0);
+            };
+            if (nphi == 4096) go(k_rows_fwd_tma<2048>, 2048);
+            else go(k_rows_fwd_tma<1024>, 1024);
+            return cudaGetLastError();
+        }
+    }
     auto go = [&](auto kern) {
         kern<<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
             x0, x1, (cplx<R> *)xh, nrows, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rscale,
@@ -609,15 +782,119 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
     }
 }
 
+template <int NC>
+__global__ void __launch_bounds__(NC / 4, 4096 / NC)
+k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ RowOut o, const float2 *__restrict__ tw,
+               const float2 *__restrict__ twp, const float *__restrict__ rcen, unsigned int *flag,
+               unsigned int *tflag, int row0)
+{
+    constexpr int N = NC, T = N / 16, PLS = row_pitch_tma(N);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    float2 *reg = reinterpret_cast<float2 *>(smem_raw + kRowHdr);
+    if (smem_u32(reg) & 127u) {                                         // TMA alignment (never expected)
+        if (threadIdx.x == 0 && tflag) atomicOr(tflag, 2u);
+        return;
+    }
+    const int q = blockIdx.y, i0 = row0 + blockIdx.x * 4;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // the column pass's output is read for the last time
+        const uint64_t pf = l2_evict_first();
+        mbar_expect_tx(bar, (unsigned)N * 32u);
+#pragma unroll
+        for (int b = 0; b < N / 256; ++b) tma_load_2d(reg + 4 * 256 * b, &tm, 2 * i0, o.src[q] * N + 256 * b, bar, pf);
+    }
+    if (!__syncthreads_and(mbar_wait_bounded(bar, 0, tflag))) return;
+    const int lane = threadIdx.x & 31, g = lane & 3, t = ((threadIdx.x >> 5) << 3) | (lane >> 2);
+    // Z'[k] = (X[k] + X*[N-k]) + i (X[k] - X*[N-k]) W^-k  (= 2 Z[k])
+    const float2 *xa = reg + 4 * t + g, *xc = reg + 4 * (N - t) + g;
+    const float2 w0 = __ldg(&tw[t]);
+    float2 v[16];
+    unroll16<0>([&](auto ec) {
+        constexpr int e = decltype(ec)::value;
+        const float2 X = xa[4 * T * e];
+        if (e == 0 && t == 0) {
+            v[e] = make_float2(X.x + X.y, X.x - X.y);
+        } else {
+            const float2 Xc = cconj(xc[-4 * T * e]);
+            v[e] = cadd(cadd(X, Xc), cmul_i(cmulc(csub(X, Xc), tw_step<e>(w0))));
+        }
+    });
+    // the exchange buffers overlay the tile; the transform synchronises
+    // before its first shared-memory write
+    fft_ct<false, N>(v, t, reg + g * PLS, twp);
+    const int i = i0 + g;
+    const float sc = o.is_phi[q] ? 1.f : 1.f / rcen[i];
+    float2 *out = reinterpret_cast<float2 *>(reinterpret_cast<float *>(o.ptr[q]) + (size_t)i * 2 * N);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        v[e] = make_float2(v[e].x * sc, v[e].y * sc);     // (y[2n], y[2n+1])
+        out[t + T * e] = v[e];
+    }
+    if (flag) {
+        bool bad = false;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) bad |= !(isfinite(v[e].x) && isfinite(v[e].y));
+        if (bad) atomicOr(flag, 1u);
+    }
+}
+
+// Tensor map of a [ncols][nr] complex FP32 intermediate (element (m, i) at
+// m nr + i) as a 2-D FP32 array [ncols][2 nr], box 8 x 256: four rows of 256
+// columns.  The driver's encoder is reached through the runtime's entry-point
+// query, so the library needs no link against the driver library.
+cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols)
+{
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Encode>(p);
+    });
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * nr, (cuuint64_t)ncols};
+    const cuuint64_t strides[1] = {(cuuint64_t)nr * 8};
+    const cuuint32_t box[2] = {8, 256}, es[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+bool rows_tma_eligible(int nr, int nphi, bool f64)
+{
+    return !f64 && BW == 1 && (nphi == 2048 || nphi == 4096) && nr % 4 == 0 && row_rpc(nphi, false) == 4;
+}
+
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
                             const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s, int row0,
-                            int nrows_run)
+                            int nrows_run, const CUtensorMap *tm, unsigned int *tflag)
 {
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
     if (nrows_run < 0) nrows_run = nr - row0;
     dim3 grid(nrows_run / rpc, o.n);
+    if constexpr (sizeof(R) == 4) {
+        if (tm && rows_tma_eligible(nr, nphi, false)) {
+            auto go = [&](auto kern, int N) {
+                kern<<<grid, N / 4, row_tma_smem_bytes(N), s>>>(*tm, o, (const float2 *)tw_row,
+                                                               (const float2 *)twp_row, rcen, flag, tflag, row0);
+            };
+            if (nphi == 4096) go(k_rows_inv_tma<2048>, 2048);
+            else go(k_rows_inv_tma<1024>, 1024);
+            return cudaGetLastError();
+        }
+    }
     auto go = [&](auto kern) {
         kern<<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
             (const cplx<R> *)oh, o, nr, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rcen, flag,
@@ -642,7 +919,9 @@ cudaError_t set_smem_limits(int max_optin)
                          (const void *)k_cols<float, 1, 2048>,    (const void *)k_cols<float, 2, 0>,
                          (const void *)k_cols<float, 2, 4096>,    (const void *)k_cols<float, 2, 2048>,
                          (const void *)k_cols<double, 1, 0>,      (const void *)k_cols<double, 2, 0>,
-                         (const void *)k_tabcols<float>,          (const void *)k_tabcols<double>};
+                         (const void *)k_tabcols<float>,          (const void *)k_tabcols<double>,
+                         (const void *)k_rows_fwd_tma<2048>,      (const void *)k_rows_fwd_tma<1024>,
+                         (const void *)k_rows_inv_tma<2048>,      (const void *)k_rows_inv_tma<1024>};
     for (const void *fn : fns) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
         if (e != cudaSuccess) return e;
@@ -651,9 +930,11 @@ cudaError_t set_smem_limits(int max_optin)
 }
 
 template cudaError_t launch_rows_fwd<float>(const float *, const float *, int, void *, int, int, const void *,
-                                            const void *, const float *, bool, cudaStream_t, int, int);
+                                            const void *, const float *, bool, cudaStream_t, int, int,
+                                            const CUtensorMap *, unsigned int *);
 template cudaError_t launch_rows_fwd<double>(const double *, const double *, int, void *, int, int, const void *,
-                                             const void *, const double *, bool, cudaStream_t, int, int);
+                                             const void *, const double *, bool, cudaStream_t, int, int,
+                                             const CUtensorMap *, unsigned int *);
 template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
                                         unsigned int *, cudaStream_t, int);
 template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
@@ -661,8 +942,10 @@ template cudaError_t launch_cols<double>(const void *, const void *, void *, int
 template cudaError_t launch_tabcols<float>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_tabcols<double>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const void *,
-                                            const float *, unsigned int *, cudaStream_t, int, int);
+                                            const float *, unsigned int *, cudaStream_t, int, int,
+                                            const CUtensorMap *, unsigned int *);
 template cudaError_t launch_rows_inv<double>(const void *, const RowOut &, int, int, const void *, const void *,
-                                             const double *, unsigned int *, cudaStream_t, int, int);
+                                             const double *, unsigned int *, cudaStream_t, int, int,
+                                             const CUtensorMap *, unsigned int *);
 
 }  // namespace sg

@@ -276,6 +276,35 @@ def test_solve_host_pipeline_equals_solve(nr, nphi, bif, dtype, outs):
             assert np.array_equal(pageable[k], ref[k].cpu().numpy()), k
 
 
+def test_input_alignment_fallback_and_rejection():
+    """The bulk-copy row transform needs 16-byte aligned inputs: an FP32 input
+    that is 8-byte but not 16-byte aligned takes the transpose-kernel row
+    transform and still meets the FP32 tolerance (and matches the aligned
+    solve to rounding); a 4-byte aligned FP32 buffer is rejected."""
+    d = rounded(inputs.ragged_noise(256, 2048, offset=5), torch.float32)
+    ref = oracle.fft64(grid(d), d.sigma_g, h_g=d.h_g, G=d.G)
+    dev = torch.device("cuda:0")
+    n = d.nr * d.nphi
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G) as plan:
+        base = torch.zeros(n + 4, device=dev)
+        base[2:2 + n] = torch.tensor(d.sigma_g.ravel(), dtype=torch.float32, device=dev)
+        x8 = base[2:2 + n].view(d.nr, d.nphi)
+        assert x8.data_ptr() % 16 == 8
+        got = plan.solve(x8)
+        torch.cuda.synchronize()
+        out = {k: v.double().cpu().numpy() for k, v in got.items()}
+        assert_close(out, ref, TOL32, "8-byte aligned input")
+        aligned = plan.solve(torch.tensor(d.sigma_g, dtype=torch.float32, device=dev))
+        torch.cuda.synchronize()
+        for k, v in aligned.items():
+            a = v.double().cpu().numpy()
+            assert np.linalg.norm(out[k] - a) <= 1e-6 * np.linalg.norm(a), k
+        x4 = base[1:1 + n].view(d.nr, d.nphi)
+        with pytest.raises(N.SgError) as e:
+            plan.solve(x4)
+        assert e.value.status == N.SG_ERR_ARG
+
+
 def test_G_and_radial_scale():
     """Linearity in G (the table scale) and radial scale invariance (App. C):
     edges x2 leave g unchanged and double Phi."""
