@@ -225,6 +225,10 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
     cudaError_t e;
     const bool ev = pl->ev[0] != nullptr;
     if (ev) cudaEventRecord(pl->ev[0], s);
+    // The column pass and the inverse rows start as programmatic dependents
+    // of the kernel before them (set-up and kernel-spectrum staging overlap
+    // its last CTAs); a stage-timed solve keeps plain stream order so that
+    // each stage's events bracket its own kernel only.
     if (pl->p.method == SG_METHOD_FFT) {
         e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row,
                                pl->twp_row, (const R *)pl->rcen, true, s, 0, -1, pl->tm_rows ? &pl->tm_sh : nullptr,
@@ -233,7 +237,8 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
         if (ev) cudaEventRecord(pl->ev[1], s);
         e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
                                          pl->flag, s)
-                       : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
+                       : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s,
+                                        0, !ev);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
         RowOut ro{};
@@ -245,7 +250,7 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
             ++ro.n;
         }
         e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, 0, -1,
-                               pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag);
+                               pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag, !ev);
         if (e != cudaSuccess) return cuda_fail(pl, e, "inverse row transform");
         if (ev) cudaEventRecord(pl->ev[3], s);
     } else {

@@ -314,55 +314,77 @@ __device__ __forceinline__ void exchange_ct(T (&v)[16], int t, T *xb)
     for (int e = 0; e < 16; ++e) v[e] = rd[e * (TT + TT / 16)];
 }
 
-// Twiddles w_r = W^{r k}, r = 1..15, of one radix-16 butterfly: six table
-// loads (r = 1, 2, 3, 4, 8, 12), the other nine as one product of two loaded
-// values each (one extra rounding), which spares the L1 data path 9 loads.
-template <typename T>
-__device__ __forceinline__ void twiddles16(const T *__restrict__ p, int Ns, T (&w)[16])
+// Base twiddles of the compile-time pass with stride Ns, loaded before the
+// exchange that precedes the pass so that their latency overlaps its
+// barriers and shared-memory traffic:
+//   radix-16 pass: W^{r k} (k = t mod Ns) for r = 1, 2, 3, 4, 8, 12; the
+//   other nine are products of two loaded values (one extra rounding), which
+//   spares the L1 data path 9 loads;
+//   final radix-RL pass: for each of its Q = 16 / RL butterflies, r = 1..4
+//   when RL = 8 (r = 5..7 as products of w4 and w1..w3), else r = 1..RL-1.
+template <int L, int Ns, typename T>
+__device__ __forceinline__ void load_pass_tw(const T *__restrict__ tp, int t, T (&b)[12])
 {
-    w[1] = __ldg(p);
-    w[2] = __ldg(p + Ns);
-    w[3] = __ldg(p + 2 * Ns);
-    w[4] = __ldg(p + 3 * Ns);
-    w[8] = __ldg(p + 7 * Ns);
-    w[12] = __ldg(p + 11 * Ns);
-    w[5] = cmul(w[4], w[1]);
-    w[6] = cmul(w[4], w[2]);
-    w[7] = cmul(w[4], w[3]);
-    w[9] = cmul(w[8], w[1]);
-    w[10] = cmul(w[8], w[2]);
-    w[11] = cmul(w[8], w[3]);
-    w[13] = cmul(w[12], w[1]);
-    w[14] = cmul(w[12], w[2]);
-    w[15] = cmul(w[12], w[3]);
+    constexpr int TT = L / 16;
+    if constexpr (Ns * 16 <= L) {
+        const T *p = tp + (t & (Ns - 1));
+        b[0] = __ldg(p);
+        b[1] = __ldg(p + Ns);
+        b[2] = __ldg(p + 2 * Ns);
+        b[3] = __ldg(p + 3 * Ns);
+        b[4] = __ldg(p + 7 * Ns);
+        b[5] = __ldg(p + 11 * Ns);
+    } else {
+        constexpr int RL = L / Ns, Q = 16 / RL, NL = RL == 8 ? 4 : RL - 1;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const T *p = tp + ((t + TT * q) & (Ns - 1));
+#pragma unroll
+            for (int r = 0; r < NL; ++r) b[q * NL + r] = __ldg(p + r * Ns);
+        }
+    }
 }
 
 template <bool FWD, int L, int Ns, typename T>
-__device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *__restrict__ tp)
+__device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *__restrict__ tp, const T (&b)[12])
 {
     constexpr int TT = L / 16;
     if constexpr (Ns * 16 <= L) {
         {
             T w[16];
-            twiddles16(tp + (t & (Ns - 1)), Ns, w);
+            w[1] = b[0];
+            w[2] = b[1];
+            w[3] = b[2];
+            w[4] = b[3];
+            w[8] = b[4];
+            w[12] = b[5];
+            w[5] = cmul(w[4], w[1]);
+            w[6] = cmul(w[4], w[2]);
+            w[7] = cmul(w[4], w[3]);
+            w[9] = cmul(w[8], w[1]);
+            w[10] = cmul(w[8], w[2]);
+            w[11] = cmul(w[8], w[3]);
+            w[13] = cmul(w[12], w[1]);
+            w[14] = cmul(w[12], w[2]);
+            w[15] = cmul(w[12], w[3]);
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[r] = twmul<FWD>(v[r], w[r]);
         }
         dft16<FWD>(v);
         if constexpr (Ns * 16 < L) {
+            T nb[12];
+            load_pass_tw<L, Ns * 16>(tp + 15 * Ns, t, nb);
             exchange_ct<Ns, TT>(v, t, xb);
-            fft_ct_pass<FWD, L, Ns * 16>(v, t, xb, tp + 15 * Ns);
+            fft_ct_pass<FWD, L, Ns * 16>(v, t, xb, tp + 15 * Ns, nb);
         }
     } else {
         constexpr int RL = L / Ns, Q = 16 / RL;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const T *p = tp + ((t + TT * q) & (Ns - 1));
             if constexpr (RL == 8) {
-                // w1..w4 loaded, w5..w7 = w4 w1..w3
                 T w[8];
 #pragma unroll
-                for (int r = 1; r <= 4; ++r) w[r] = __ldg(p + (r - 1) * Ns);
+                for (int r = 1; r <= 4; ++r) w[r] = b[q * 4 + r - 1];
                 w[5] = cmul(w[4], w[1]);
                 w[6] = cmul(w[4], w[2]);
                 w[7] = cmul(w[4], w[3]);
@@ -370,7 +392,7 @@ __device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *_
                 for (int r = 1; r < 8; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], w[r]);
             } else {
 #pragma unroll
-                for (int r = 1; r < RL; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], __ldg(p + (r - 1) * Ns));
+                for (int r = 1; r < RL; ++r) v[q + r * Q] = twmul<FWD>(v[q + r * Q], b[q * (RL - 1) + r - 1]);
             }
         }
         if constexpr (RL == 2) {
@@ -391,8 +413,10 @@ __device__ __forceinline__ void fft_ct(T (&v)[16], int t, T *xb, const T *__rest
 {
     static_assert(L >= 256 && (L & (L - 1)) == 0, "compile-time FFT needs a power of two >= 256");
     dft16<FWD>(v);
+    T b[12];
+    load_pass_tw<L, 16>(twp, t, b);
     exchange_ct<1, L / 16>(v, t, xb);
-    fft_ct_pass<FWD, L, 16>(v, t, xb, twp);
+    fft_ct_pass<FWD, L, 16>(v, t, xb, twp, b);
 }
 
 // Compile-time length when LC > 0, runtime length L otherwise.

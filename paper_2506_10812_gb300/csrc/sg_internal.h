@@ -60,10 +60,13 @@ bool rows_tma_eligible(int nr, int nphi, bool f64);
 // products with the packed kernel spectra, inverse FFT of every requested
 // (target, component), rows 0..nr-1 kept.
 // flag: bit 2 set when a staged copy never completed (bounded wait).
-// ncols > 0: only columns 0 .. ncols - 1.
+// ncols > 0: only columns 0 .. ncols - 1.  pdl: programmatic dependent
+// launch on the row transform before it (the set-up and the first kernel-
+// spectrum copies overlap that kernel's last CTAs).
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
-                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols = 0);
+                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols = 0,
+                        bool pdl = false);
 
 // Column pass with tensor-core DFT stages (sg_dftmma.cu): FP32 gas-only
 // plans with 2 nr in {2048, 4096}; engine 1..4 as SG_ENGINE_DFT_*; atab
@@ -93,11 +96,13 @@ struct RowOut {
 // check into *flag bit 1 when flag != NULL).
 // tm: the tensor map of oh (all nsrc * 3 spectra); with it, FP32 rows of the
 // hot lengths load their tiles by bulk tensor copies (bit 2 of *tflag when a
-// copy never completed).
+// copy never completed).  pdl: programmatic dependent launch on the column
+// pass before it.
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
                             const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s, int row0 = 0,
-                            int nrows_run = -1, const CUtensorMap *tm = nullptr, unsigned int *tflag = nullptr);
+                            int nrows_run = -1, const CUtensorMap *tm = nullptr, unsigned int *tflag = nullptr,
+                            bool pdl = false);
 
 // Indirect term (App. E): out[2 a + {0, 1}] = (A_a, B_a) in FP64; partial
 // holds indirect_blocks(nphi) x 4 doubles.

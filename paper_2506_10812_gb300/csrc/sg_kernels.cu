@@ -42,6 +42,7 @@
 
 #include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "sg_bessel.cuh"
 #include "sg_fft.cuh"
@@ -50,6 +51,28 @@
 
 namespace sg {
 
+
+// Launch with the programmatic-stream-serialization attribute when pdl:
+// the kernel may then start before its predecessor on the stream finishes,
+// and must call griddep_wait before reading anything that predecessor
+// writes, and read it coherently (ld_cg_hint or TMA, never the
+// non-coherent path, which presumes data fixed for the kernel's lifetime).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                      Args &&...args)
+{
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // ----------------------------------------------------------------- sizes
 // Rows per CTA of the row transforms: up to SG_ROW_RPC (4; 8 measured
@@ -221,6 +244,7 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
 {
     constexpr int N = NC, T = N / 16, NW = T / 8, PLS = row_pitch_tma(N), XS = T + T / 16;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    griddep_launch();                     // the column pass may set up once every row CTA runs
     float *red = reinterpret_cast<float *>(smem_raw + 64);              // NW x 4 partial sums
     float2 *reg = reinterpret_cast<float2 *>(smem_raw + kRowHdr);
     if (smem_u32(reg) & 127u) {                                         // TMA alignment (never expected)
@@ -231,6 +255,7 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
     const int a = blockIdx.y, i0 = row0 + blockIdx.x * 4, i = i0 + g;
     const float *xa = a == 0 ? x0 : x1;
     const float sc = rscale ? rscale[i] : 1.f;
+    const float2 w0 = __ldg(&tw[t]);                     // R2C twiddle base, used after the transform
     float2 v[16];
     {
         // the four rows (contiguous) land at a pitch of N + 4 complex, which
@@ -281,7 +306,6 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
     for (int e = 0; e < 16; ++e) zs[e * XS] = v[e];
     __syncthreads();
     const float2 *zc = xb + (N - t) + (N >> 4) + ((-t) >> 4);   // pidx(N - k) = zc - e XS
-    const float2 w0 = __ldg(&tw[t]);
     unroll16<0>([&](auto ec) {
         constexpr int e = decltype(ec)::value;
         const float2 Z = v[e];
@@ -324,6 +348,7 @@ k_rows_fwd(const R *__restrict__ x0, const R *__restrict__ x1, cplx<R> *__restri
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *red = reinterpret_cast<R *>(smem_raw);                 // 64 reals: per-warp partial sums
     C *sm = reinterpret_cast<C *>(smem_raw + 64 * sizeof(double));
+    griddep_launch();
     const int nphi = NC > 0 ? 2 * NC : nphi_rt;
     const int N = nphi >> 1, T = N >> 4;
     if (NC > 0) rpc = row_rpc_of(2 * NC, sizeof(C));           // compile-time for the hot lengths
@@ -473,7 +498,7 @@ __device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cpl
     for (int a = 0; a < NS; ++a) {
         const C *col = sh + (size_t)a * N * nr;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = col[blk(0, t + T * e, nr)];
+        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(col + blk(0, t + T * e, nr), l2_evict_first());
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
         fft_reg<true>(v, L, T, t, xb, tw);
@@ -524,8 +549,10 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
     C *xb = reinterpret_cast<C *>(smem_raw + 16);
     C *tb = reinterpret_cast<C *>(smem_raw + 16 + align16((size_t)padded_len(L) * sizeof(C)));
     const int t = threadIdx.x, m = blockIdx.x;
+    griddep_launch();                     // the inverse rows may set up once every column CTA runs
     if (m == 0) {
         // column 0 keeps its source spectra in the table area
+        griddep_wait();
         col0_path<R, NS>(sh, tab, oh, nr, N, outmask, tw, xb, tb);
         return;
     }
@@ -551,6 +578,7 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
     if (t == 0) mbar_init(bar, 1);
     __syncthreads();
     issue(0);                                      // lands while the forward FFTs run
+    griddep_wait();                                // the row spectra are complete from here on
 
     C v[16];
     C spec[NS == 1 ? 16 : 1];                      // NS == 1: source spectrum in registers
@@ -558,7 +586,7 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
     for (int a = 0; a < NS; ++a) {
         const uint64_t pf = l2_evict_first();
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = ld_hint(sh + (size_t)a * N * nr + blk(m, t + T * e, nr), pf);
+        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(sh + (size_t)a * N * nr + blk(m, t + T * e, nr), pf);
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
         fft_any<true, LC>(v, L, T, t, xb, tw);
@@ -612,15 +640,16 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
 
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
-                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols)
+                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols, bool pdl)
 {
     const bool f64 = sizeof(R) == 8;
     const int N = nphi / 2, T = (2 * nr) / 16;
     const size_t smem = col_smem_bytes(nr, nsrc, f64);
     const int grid = ncols > 0 && ncols < N ? ncols : N;
+    cudaError_t err = cudaSuccess;
     auto go = [&](auto kern) {
-        kern<<<grid, T, smem, s>>>((const cplx<R> *)sh, (const cplx<R> *)tab, (cplx<R> *)oh, nr, N, outmask,
-                                (const cplx<R> *)tw_col, flag);
+        err = launch_ex(kern, dim3(grid), dim3(T), smem, s, pdl, (const cplx<R> *)sh, (const cplx<R> *)tab,
+                        (cplx<R> *)oh, nr, N, outmask, (const cplx<R> *)tw_col, flag);
     };
     const int L = 2 * nr;
     if (nsrc == 1) {
@@ -632,7 +661,7 @@ cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int n
         else if (!f64 && L == 2048) go(k_cols<R, 2, 2048>);
         else go(k_cols<R, 2, 0>);
     }
-    return cudaGetLastError();
+    return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 // ------------------------------------------- table column FFT + packing
@@ -709,6 +738,7 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
     const int q = blockIdx.y;
     const int i0 = row0 + blockIdx.x * rpc;
     const C *src = oh + (size_t)o.src[q] * N * nrows;
+    griddep_wait();                       // the column pass's output is complete from here on
     // FAST: as in k_rows_fwd, per-thread bases plus compile-time offsets
     constexpr bool FAST = NC >= 256 && BW == 1 && row_rpc_of(2 * NC, sizeof(C)) == 4;
     const uint64_t pf = l2_evict_first();
@@ -719,7 +749,7 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
         const C *s0 = src + (size_t)m0 * nrows + i0 + gg;
         C tmp[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) tmp[j] = ld_hint(s0 + (size_t)j * (nthr / 4) * nrows, pf);
+        for (int j = 0; j < 16; ++j) tmp[j] = ld_cg_hint(s0 + (size_t)j * (nthr / 4) * nrows, pf);
         const int sb0 = 4 * m0 + (gg ^ ((m0 >> 2) & 3));
 #pragma unroll
         for (int j = 0; j < 16; ++j) sm[sb0 + j * nthr] = tmp[j];
@@ -733,7 +763,7 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
             const int idx = threadIdx.x + j * blockDim.x;
             const int bb = idx / per, rem = idx - bb * per;
             const int gg = rem / BW, c = rem - gg * BW;
-            tmp[j] = ld_hint(src + ((size_t)bb * nrows + i0 + gg) * BW + c, pf);
+            tmp[j] = ld_cg_hint(src + ((size_t)bb * nrows + i0 + gg) * BW + c, pf);
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -797,8 +827,13 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
         return;
     }
     const int q = blockIdx.y, i0 = row0 + blockIdx.x * 4;
+    const int lane = threadIdx.x & 31, g = lane & 3, t = ((threadIdx.x >> 5) << 3) | (lane >> 2);
+    // plan constants, loaded while the tile is in flight
+    const float2 w0 = __ldg(&tw[t]);
+    const float sc = o.is_phi[q] ? 1.f : 1.f / __ldg(&rcen[i0 + g]);
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
+    griddep_wait();                       // the column pass's output is complete from here on
     if (threadIdx.x == 0) {
         // the column pass's output is read for the last time
         const uint64_t pf = l2_evict_first();
@@ -807,10 +842,8 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
         for (int b = 0; b < N / 256; ++b) tma_load_2d(reg + 4 * 256 * b, &tm, 2 * i0, o.src[q] * N + 256 * b, bar, pf);
     }
     if (!__syncthreads_and(mbar_wait_bounded(bar, 0, tflag))) return;
-    const int lane = threadIdx.x & 31, g = lane & 3, t = ((threadIdx.x >> 5) << 3) | (lane >> 2);
     // Z'[k] = (X[k] + X*[N-k]) + i (X[k] - X*[N-k]) W^-k  (= 2 Z[k])
     const float2 *xa = reg + 4 * t + g, *xc = reg + 4 * (N - t) + g;
-    const float2 w0 = __ldg(&tw[t]);
     float2 v[16];
     unroll16<0>([&](auto ec) {
         constexpr int e = decltype(ec)::value;
@@ -826,7 +859,6 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
     // before its first shared-memory write
     fft_ct<false, N>(v, t, reg + g * PLS, twp);
     const int i = i0 + g;
-    const float sc = o.is_phi[q] ? 1.f : 1.f / rcen[i];
     float2 *out = reinterpret_cast<float2 *>(reinterpret_cast<float *>(o.ptr[q]) + (size_t)i * 2 * N);
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
@@ -878,8 +910,9 @@ bool rows_tma_eligible(int nr, int nphi, bool f64)
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
                             const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s, int row0,
-                            int nrows_run, const CUtensorMap *tm, unsigned int *tflag)
+                            int nrows_run, const CUtensorMap *tm, unsigned int *tflag, bool pdl)
 {
+    cudaError_t err = cudaSuccess;
     const bool f64 = sizeof(R) == 8;
     const int rpc = row_rpc(nphi, f64);
     if (nrows_run < 0) nrows_run = nr - row0;
@@ -887,23 +920,23 @@ cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, c
     if constexpr (sizeof(R) == 4) {
         if (tm && rows_tma_eligible(nr, nphi, false)) {
             auto go = [&](auto kern, int N) {
-                kern<<<grid, N / 4, row_tma_smem_bytes(N), s>>>(*tm, o, (const float2 *)tw_row,
-                                                               (const float2 *)twp_row, rcen, flag, tflag, row0);
+                err = launch_ex(kern, grid, dim3(N / 4), row_tma_smem_bytes(N), s, pdl, *tm, o,
+                                (const float2 *)tw_row, (const float2 *)twp_row, rcen, flag, tflag, row0);
             };
             if (nphi == 4096) go(k_rows_inv_tma<2048>, 2048);
             else go(k_rows_inv_tma<1024>, 1024);
-            return cudaGetLastError();
+            return err != cudaSuccess ? err : cudaGetLastError();
         }
     }
     auto go = [&](auto kern) {
-        kern<<<grid, (nphi / 32) * rpc, row_smem_bytes(nphi, rpc, f64), s>>>(
-            (const cplx<R> *)oh, o, nr, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rcen, flag,
-            row0);
+        err = launch_ex(kern, grid, dim3((nphi / 32) * rpc), row_smem_bytes(nphi, rpc, f64), s, pdl,
+                        (const cplx<R> *)oh, o, nr, nphi, rpc, (const cplx<R> *)tw_row, (const cplx<R> *)twp_row, rcen,
+                        flag, row0);
     };
     if (!f64 && nphi == 4096) go(k_rows_inv<R, 2048>);
     else if (!f64 && nphi == 2048) go(k_rows_inv<R, 1024>);
     else go(k_rows_inv<R, 0>);
-    return cudaGetLastError();
+    return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 // Raise every kernel's dynamic shared-memory limit to the device maximum
@@ -936,16 +969,16 @@ template cudaError_t launch_rows_fwd<double>(const double *, const double *, int
                                              const void *, const double *, bool, cudaStream_t, int, int,
                                              const CUtensorMap *, unsigned int *);
 template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
-                                        unsigned int *, cudaStream_t, int);
+                                        unsigned int *, cudaStream_t, int, bool);
 template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
-                                         unsigned int *, cudaStream_t, int);
+                                         unsigned int *, cudaStream_t, int, bool);
 template cudaError_t launch_tabcols<float>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_tabcols<double>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const void *,
                                             const float *, unsigned int *, cudaStream_t, int, int,
-                                            const CUtensorMap *, unsigned int *);
+                                            const CUtensorMap *, unsigned int *, bool);
 template cudaError_t launch_rows_inv<double>(const void *, const RowOut &, int, int, const void *, const void *,
                                              const double *, unsigned int *, cudaStream_t, int, int,
-                                             const CUtensorMap *, unsigned int *);
+                                             const CUtensorMap *, unsigned int *, bool);
 
 }  // namespace sg

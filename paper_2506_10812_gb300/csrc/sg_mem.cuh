@@ -100,6 +100,14 @@ __device__ __forceinline__ double2 ld_cg_hint(const double2 *p, uint64_t pol)
     return v;
 }
 
+// ------------------------------------------ programmatic dependent launch
+// griddep_wait: until the grids this launch depends on programmatically have
+// completed and their memory is visible (returns at once for an ordinary
+// launch); every thread that reads their output calls it first.
+// griddep_launch: this CTA lets the dependent grid start launching.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------- TMA bulk copy + mbarrier
 __device__ __forceinline__ unsigned smem_u32(const void *p)
 {

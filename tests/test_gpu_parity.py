@@ -305,6 +305,38 @@ def test_input_alignment_fallback_and_rejection():
         assert e.value.status == N.SG_ERR_ARG
 
 
+@pytest.mark.parametrize("nr,nphi,bif,dtype", [
+    (32, 64, False, torch.float64),       # transpose-kernel rows, runtime-length columns
+    (128, 2048, False, torch.float32),    # tensor-copy rows, runtime-length columns
+    (1024, 4096, False, torch.float32),   # tensor-copy rows, compile-time columns of 2048
+    (64, 2048, True, torch.float32)])     # gas + dust
+def test_back_to_back_solves_are_deterministic(nr, nphi, bif, dtype):
+    """The column pass and the inverse rows start as programmatic dependents
+    of the kernel before them.  Twenty back-to-back solves of two alternating
+    inputs, with no synchronisation in between, each equal their single-solve
+    result bit for bit (a read of an unfinished predecessor's output would
+    show up as a mismatch)."""
+    dev = torch.device("cuda:0")
+    A = inputs.ragged_noise(nr, nphi, bifluid=bif, offset=31)
+    B = inputs.ragged_noise(nr, nphi, bifluid=bif, offset=32)
+    t = lambda x: None if x is None else torch.tensor(x, dtype=dtype, device=dev)
+    with P()(nr, nphi, A.r_in, A.r_out, A.h_g, A.h_d, G=A.G, dtype=dtype) as plan:
+        ins = [(t(A.sigma_g), t(A.sigma_d)), (t(B.sigma_g), t(B.sigma_d))]
+        refs = []
+        for sg, sd in ins:
+            refs.append({k: v.clone() for k, v in plan.solve(sg, sd).items()})
+            torch.cuda.synchronize()
+        outs = [[{k: torch.empty_like(v) for k, v in refs[j].items()} for j in range(2)] for _ in range(10)]
+        for it in range(10):
+            for j, (sg, sd) in enumerate(ins):
+                plan.solve(sg, sd, out=outs[it][j])
+        torch.cuda.synchronize()
+        for it in range(10):
+            for j in range(2):
+                for k, v in refs[j].items():
+                    assert torch.equal(outs[it][j][k], v), (it, j, k)
+
+
 def test_G_and_radial_scale():
     """Linearity in G (the table scale) and radial scale invariance (App. C):
     edges x2 leave g unchanged and double Phi."""
