@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--nr", type=int, default=2048)
     ap.add_argument("--nphi", type=int, default=4096)
     ap.add_argument("--bifluid", action="store_true", help="gas + dust (St = 0.1) instead of gas only")
+    ap.add_argument("--outputs", default="phi,gr,gphi",
+                    help="components per fluid: phi,gr,gphi (default) or gr,gphi (accelerations only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batch", action="store_true",
@@ -61,7 +63,9 @@ def parse():
     ap.add_argument("--engine", default="fft32",
                     choices=("fft32", "dft_fp16x3", "dft_bf16x3", "dft_fp16", "dft_bf16"),
                     help="column-pass engine (tensor-core DFT stages for the precision study; gas-only discs)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    outputs_of(args)          # reject a bad --outputs before any device work
+    return args
 
 
 def workload(args, rank=0):
@@ -71,9 +75,19 @@ def workload(args, rank=0):
     return inputs.lognormal_gas(args.nr, args.nphi, offset=2 + 1000 * rank)
 
 
+_COMP_NAMES = {"phi": "Phi", "gr": "g_r", "gphi": "g_phi"}
+
+
+def outputs_of(args):
+    outs = tuple(x.strip() for x in args.outputs.split(",") if x.strip())
+    if not outs or any(x not in _COMP_NAMES for x in outs) or len(set(outs)) != len(outs):
+        raise SystemExit(f"--outputs: a comma list of distinct phi, gr, gphi (got {args.outputs!r})")
+    return outs
+
+
 def config_of(args, d):
     return {"workload": d.label + f", h_g={d.h_g}" + (f", h_d={d.h_d:.4g}" if d.h_d else "")
-            + ", FFT path, outputs Phi + g_r + g_phi per fluid",
+            + ", FFT path, outputs " + " + ".join(_COMP_NAMES[x] for x in outputs_of(args)) + " per fluid",
             "nr": d.nr, "nphi": d.nphi, "r_in": d.r_in, "r_out": d.r_out,
             "fluids": 2 if d.sigma_d is not None else 1,
             "l2": "flushed between timed steps (256 MiB write)",
@@ -258,7 +272,7 @@ def run_ours(args):
         plan.set_column_engine(args.engine)
     sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
     sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=torch.float32, device=dev)
-    out = plan.solve(sg, sd)
+    out = plan.solve(sg, sd, outputs=outputs_of(args))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     K, W = args.steps, args.warmup
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(K)]
@@ -308,7 +322,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (the column pass)
     nsrc = 2 if d.sigma_d is not None else 1
-    ncomp = 3
+    ncomp = len(outputs_of(args))
     N, nr = d.nphi // 2, d.nr
     col_bytes = 8 * (nsrc * N * nr + nsrc * nsrc * ncomp * (N + 1) * nr + nsrc * ncomp * N * nr)
     col_ms = statistics.mean(stage["cols"])
@@ -324,6 +338,8 @@ def run_ours(args):
     # the row spectra written, the column output read back and the outputs written
     step_bytes = col_bytes + 8 * nsrc * N * nr + 4 * nsrc * d.cells + 8 * nsrc * ncomp * N * nr + 4 * nsrc * ncomp * d.cells
     step_frac = step_bytes / (ms_per_step * 1e-3) / 1e9 / peak
+    # compulsory traffic: the sources, the kernel spectra and the outputs (28 B/cell gas-only with Phi)
+    min_bytes = 4 * nsrc * d.cells + 8 * nsrc * nsrc * ncomp * (N + 1) * nr + 4 * nsrc * ncomp * d.cells
 
     # ---- end to end through the C ABI with host buffers (pinned)
     hin_g = torch.from_numpy(d.sigma_g.astype(np.float32)).pin_memory()
@@ -347,7 +363,10 @@ def run_ours(args):
               "config": dict(config_of(args, d), **({} if args.engine == "fft32" else {"column_engine": args.engine})),
               "roofline": roofline,
               "step_roofline": {"model_bytes_per_step": step_bytes, "frac": round(step_frac, 4),
-                                "note": "3-pass traffic model over the whole step"},
+                                "compulsory_bytes_per_step": min_bytes,
+                                "compulsory_frac": round(min_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
+                                "note": "3-pass traffic model over the whole step; compulsory = sources + "
+                                        "kernel spectra + outputs"},
               "stages_ms": {k: statistics.mean(v) for k, v in stage.items()},
               "plan_build_ms": plan_build_ms,
               "e2e": {"value": cells_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,

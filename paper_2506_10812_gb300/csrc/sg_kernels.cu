@@ -104,6 +104,9 @@ size_t col_smem_bytes(int nr, int nsrc, bool f64)
     const size_t esz = f64 ? 16 : 8;
     const int L = 2 * nr;
     const size_t xb = align16((size_t)padded_len(L) * esz);
+    // FP32 gas + dust: one (target, component) step of kernel spectra staged
+    // at a time, source spectra in registers, column 0 recomputed per step
+    if (nsrc == 2 && !f64) return 16 + xb + (size_t)2 * tab_pitch(nr) * esz;
     const size_t tb = (size_t)nsrc * 3 * tab_pitch(nr) * esz;
     const size_t spec = nsrc == 2 ? (size_t)2 * L * esz : 0;   // gas + dust spectra live in shared memory
     // column 0 keeps its source spectra in the table area instead
@@ -536,6 +539,142 @@ __device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cpl
 }
 
 // LC > 0: compile-time column length (2 nr).
+// Column 0 of an FP32 gas + dust plan without shared-memory source spectra:
+// each requested (target, component) step transforms the two packed source
+// columns again and pairs Z(k) with Z*(L - k) through the exchange buffer.
+// The same terms in the same order as col0_path, so the same result; 18
+// transforms instead of 8, in one CTA of the first wave.
+template <typename R>
+__device__ __noinline__ void col0_recompute(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
+                                            cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
+                                            const cplx<R> *__restrict__ tw, cplx<R> *xb)
+{
+    using C = cplx<R>;
+    constexpr int NS = 2;
+    const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
+    const int t = threadIdx.x;
+    for (int q = 0; q < 3 * NS; ++q) {
+        if (!((outmask >> q) & 1u)) continue;
+        const int b = q / 3, c = q % 3;
+        C acc[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) acc[e] = mkc<C>(0, 0);
+        for (int a = 0; a < NS; ++a) {
+            C v[16];
+            const C *col = sh + (size_t)a * N * nr;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(col + blk(0, t + T * e, nr), l2_evict_first());
+#pragma unroll
+            for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
+            fft_reg<true>(v, L, T, t, xb, tw);
+            __syncthreads();                   // the transform's last exchange reads are done
+#pragma unroll
+            for (int e = 0; e < 16; ++e) xb[pidx(t + T * e)] = v[e];
+            __syncthreads();
+            const C *t0 = tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1)) * P;
+            const C *tn = t0 + (size_t)N * P;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int k = t + T * e;
+                const C Z = v[e];
+                const C Zm = cconj(xb[pidx((L - k) & (L - 1))]);
+                C S0 = spec_at(t0, k, H, e >= 8), SN = spec_at(tn, k, H, e >= 8);
+                if (c == 2) {
+                    S0 = cmul_mi(S0);
+                    SN = cmul_mi(SN);
+                }
+                acc[e] = cadd(acc[e], cscale(cadd(cmul(cadd(Z, Zm), S0), cmul(csub(Z, Zm), SN)), (R)0.5));
+            }
+            __syncthreads();                   // before the next transform rewrites the buffer
+        }
+        fft_reg<false>(acc, L, T, t, xb, tw);
+        C *o = oh + (size_t)(b * 3 + c) * N * nr;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[blk(0, t + T * e, nr)] = acc[e];
+    }
+}
+
+// Columns m >= 1 of an FP32 gas + dust plan: both source spectra stay in
+// registers, and the kernel spectra of one (target, component) step (one per
+// source) are staged at a time; the next step's copy is issued once the
+// products have read the buffer, so it lands during the inverse transform.
+// 2 CTAs per SM instead of 1 (83.6 KB of shared memory at 2 nr = 4096).
+template <typename R, int LC>
+__device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
+                                                cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
+                                                const cplx<R> *__restrict__ tw, unsigned int *flag, cplx<R> *xb,
+                                                cplx<R> *tb, uint64_t *bar, int m)
+{
+    using C = cplx<R>;
+    constexpr int NS = 2;
+    const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
+    const int t = threadIdx.x;
+    auto next_q = [&](int q) {
+        for (++q; q < 3 * NS; ++q)
+            if ((outmask >> q) & 1u) return q;
+        return -1;
+    };
+    auto issue = [&](int q) {
+        if (t == 0) {
+            const int b = q / 3, c = q % 3;
+            const uint64_t pol = l2_evict_first();
+            mbar_expect_tx(bar, (unsigned)(NS * P * sizeof(C)));
+#pragma unroll
+            for (int a = 0; a < NS; ++a)
+                tma_load_1d(tb + (size_t)a * P, tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1) + m) * P,
+                            P * sizeof(C), bar, pol);
+        }
+    };
+    int q = next_q(-1);
+    if (t == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (q >= 0) issue(q);                          // lands while the forward FFTs run
+    griddep_wait();                                // the row spectra are complete from here on
+    C spec[NS][16];
+#pragma unroll
+    for (int a = 0; a < NS; ++a) {
+        C v[16];
+        const uint64_t pf = l2_evict_first();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(sh + (size_t)a * N * nr + blk(m, t + T * e, nr), pf);
+#pragma unroll
+        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
+        fft_any<true, LC>(v, L, T, t, xb, tw);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) spec[a][e] = v[e];
+    }
+    for (int s = 0; q >= 0; ++s) {
+        const int b = q / 3, c = q % 3;
+        if (__syncthreads_or(!mbar_wait_bounded(bar, (unsigned)(s & 1), flag))) return;
+        C v[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int k = t + T * e;
+            C acc = mkc<C>(0, 0);
+#pragma unroll
+            for (int a = 0; a < NS; ++a) {
+                C S = spec_at(tb + (size_t)a * P, k, H, e >= 8);
+                if (c == 2) S = cmul_mi(S);                   // K_phi spectrum = -i S
+                acc = cfma(spec[a][e], S, acc);
+            }
+            v[e] = acc;
+        }
+        const int qn = next_q(q);
+        if (qn >= 0) {
+            // every read of this step's spectra precedes the TMA rewrite
+            __syncthreads();
+            fence_proxy_async();
+            issue(qn);
+        }
+        fft_any<false, LC>(v, L, T, t, xb, tw);
+        C *o = oh + (size_t)(b * 3 + c) * N * nr;
+        const uint64_t pl = l2_evict_last();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) st_hint(o + blk(m, t + T * e, nr), v[e], pl);   // rows 0..nr-1 only
+        q = qn;
+    }
+}
+
 template <typename R, int NS, int LC>
 __global__ void __launch_bounds__(512)
 k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr_rt,
@@ -550,10 +689,17 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
     C *tb = reinterpret_cast<C *>(smem_raw + 16 + align16((size_t)padded_len(L) * sizeof(C)));
     const int t = threadIdx.x, m = blockIdx.x;
     griddep_launch();                     // the inverse rows may set up once every column CTA runs
+    constexpr bool PAIR = NS == 2 && sizeof(R) == 4;
     if (m == 0) {
-        // column 0 keeps its source spectra in the table area
+        // column 0 keeps its source spectra in the table area (recomputed
+        // per step for FP32 gas + dust)
         griddep_wait();
-        col0_path<R, NS>(sh, tab, oh, nr, N, outmask, tw, xb, tb);
+        if constexpr (PAIR) col0_recompute<R>(sh, tab, oh, nr, N, outmask, tw, xb);
+        else col0_path<R, NS>(sh, tab, oh, nr, N, outmask, tw, xb, tb);
+        return;
+    }
+    if constexpr (PAIR) {
+        cols_pair_steps<R, LC>(sh, tab, oh, nr, N, outmask, tw, flag, xb, tb, bar, m);
         return;
     }
     C *sspec = tb + (size_t)NS * 3 * P;           // NS == 2: source spectra in shared memory
