@@ -99,6 +99,30 @@ size_t row_smem_bytes(int nphi, int rpc, bool f64)
 
 __host__ __device__ static inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+// Kernel spectra staged one (target, component) step at a time (cols_pair_steps):
+// every FP32 gas + dust plan, and FP32 gas-only columns of length 4096, which
+// then fit 80 registers and run 3 CTAs of 256 threads per SM instead of 2
+// (column pass 74.4 -> 70.2 us on the 2048 x 4096 disc).  At length 2048 (1.1
+// waves of 6 CTAs per SM) the exposed per-step copy waits made it slower
+// (22.3 -> 28.7 us), so those columns keep all three tables staged at once.
+#ifndef SG_COLS_GAS_STEPS
+#define SG_COLS_GAS_STEPS 1
+#endif
+__host__ __device__ constexpr bool cols_steps(int nsrc, bool f64, int L)
+{
+    return !f64 && (nsrc == 2 || (SG_COLS_GAS_STEPS && nsrc == 1 && L == 4096));
+}
+// launch bounds of k_cols<R, NS, LC>: 768 threads per SM for the staged
+// gas-only lengths, otherwise up to 512 threads (128 registers each)
+constexpr int cols_max_threads(int ns, bool f64, int lc)
+{
+    return ns == 1 && cols_steps(1, f64, lc) ? lc / 16 : 512;
+}
+constexpr int cols_min_blocks(int ns, bool f64, int lc)
+{
+    return ns == 1 && cols_steps(1, f64, lc) ? 768 / (lc / 16) : 1;
+}
+
 size_t col_smem_bytes(int nr, int nsrc, bool f64)
 {
     const size_t esz = f64 ? 16 : 8;
@@ -106,7 +130,7 @@ size_t col_smem_bytes(int nr, int nsrc, bool f64)
     const size_t xb = align16((size_t)padded_len(L) * esz);
     // FP32 gas + dust: one (target, component) step of kernel spectra staged
     // at a time, source spectra in registers, column 0 recomputed per step
-    if (nsrc == 2 && !f64) return 16 + xb + (size_t)2 * tab_pitch(nr) * esz;
+    if (cols_steps(nsrc, f64, L)) return 16 + xb + (size_t)nsrc * tab_pitch(nr) * esz;
     const size_t tb = (size_t)nsrc * 3 * tab_pitch(nr) * esz;
     const size_t spec = nsrc == 2 ? (size_t)2 * L * esz : 0;   // gas + dust spectra live in shared memory
     // column 0 keeps its source spectra in the table area instead
@@ -539,18 +563,18 @@ __device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cpl
 }
 
 // LC > 0: compile-time column length (2 nr).
-// Column 0 of an FP32 gas + dust plan without shared-memory source spectra:
-// each requested (target, component) step transforms the two packed source
-// columns again and pairs Z(k) with Z*(L - k) through the exchange buffer.
-// The same terms in the same order as col0_path, so the same result; 18
-// transforms instead of 8, in one CTA of the first wave.
-template <typename R>
+// Column 0 of a plan that stages kernel spectra per step (no shared-memory
+// source spectra): each requested (target, component) step transforms the
+// packed source columns again and pairs Z(k) with Z*(L - k) through the
+// exchange buffer.  The same terms in the same order as col0_path, so the
+// same result; for gas + dust 18 transforms instead of 8, in one CTA of the
+// first wave.
+template <typename R, int NS>
 __device__ __noinline__ void col0_recompute(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
                                             cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
                                             const cplx<R> *__restrict__ tw, cplx<R> *xb)
 {
     using C = cplx<R>;
-    constexpr int NS = 2;
     const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
     const int t = threadIdx.x;
     for (int q = 0; q < 3 * NS; ++q) {
@@ -598,15 +622,14 @@ __device__ __noinline__ void col0_recompute(const cplx<R> *__restrict__ sh, cons
 // registers, and the kernel spectra of one (target, component) step (one per
 // source) are staged at a time; the next step's copy is issued once the
 // products have read the buffer, so it lands during the inverse transform.
-// 2 CTAs per SM instead of 1 (83.6 KB of shared memory at 2 nr = 4096).
-template <typename R, int LC>
+// 2 CTAs per SM instead of 1 (66 KB of shared memory at 2 nr = 4096).
+template <typename R, int LC, int NS>
 __device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
                                                 cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
                                                 const cplx<R> *__restrict__ tw, unsigned int *flag, cplx<R> *xb,
                                                 cplx<R> *tb, uint64_t *bar, int m)
 {
     using C = cplx<R>;
-    constexpr int NS = 2;
     const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
     const int t = threadIdx.x;
     auto next_q = [&](int q) {
@@ -676,7 +699,7 @@ __device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, 
 }
 
 template <typename R, int NS, int LC>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(cols_max_threads(NS, sizeof(R) == 8, LC), cols_min_blocks(NS, sizeof(R) == 8, LC))
 k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr_rt,
        int N, uint32_t outmask, const cplx<R> *__restrict__ tw, unsigned int *flag)
 {
@@ -689,17 +712,17 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
     C *tb = reinterpret_cast<C *>(smem_raw + 16 + align16((size_t)padded_len(L) * sizeof(C)));
     const int t = threadIdx.x, m = blockIdx.x;
     griddep_launch();                     // the inverse rows may set up once every column CTA runs
-    constexpr bool PAIR = NS == 2 && sizeof(R) == 4;
+    constexpr bool PAIR = NS == 2 ? sizeof(R) == 4 : cols_steps(1, sizeof(R) == 8, LC);
     if (m == 0) {
         // column 0 keeps its source spectra in the table area (recomputed
         // per step for FP32 gas + dust)
         griddep_wait();
-        if constexpr (PAIR) col0_recompute<R>(sh, tab, oh, nr, N, outmask, tw, xb);
+        if constexpr (PAIR) col0_recompute<R, NS>(sh, tab, oh, nr, N, outmask, tw, xb);
         else col0_path<R, NS>(sh, tab, oh, nr, N, outmask, tw, xb, tb);
         return;
     }
     if constexpr (PAIR) {
-        cols_pair_steps<R, LC>(sh, tab, oh, nr, N, outmask, tw, flag, xb, tb, bar, m);
+        cols_pair_steps<R, LC, NS>(sh, tab, oh, nr, N, outmask, tw, flag, xb, tb, bar, m);
         return;
     }
     C *sspec = tb + (size_t)NS * 3 * P;           // NS == 2: source spectra in shared memory
