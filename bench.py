@@ -55,7 +55,8 @@ def parse():
                     help="64 uneven gas + dust discs per step instead of one 2048 x 4096 disc")
     ap.add_argument("--batch-n", type=int, default=64, help="discs in the batch (the first n of the 64)")
     ap.add_argument("--batch-config", default="auto",
-                    help="'auto' (autotune) or threads,ctas_per_sm,order,specialize (e.g. 256,2,staged,1)")
+                    help="'auto' (autotune both engines), threads,ctas_per_sm,order,specialize for the persistent "
+                         "kernel (e.g. 256,2,staged,1), or streams:K for the stream engine")
     ap.add_argument("--no-loop", action="store_true", help="batch mode: skip timing the per-disc loops")
     ap.add_argument("--surrogate", action="store_true",
                     help="train the neural-operator surrogate on 512 x 1024 fields and report it against the exact path")
@@ -449,6 +450,8 @@ def run_batch(args):
     t0 = time.perf_counter()
     if args.batch_config == "auto":
         batch = Batch(plans, sg, sd, outs, autotune=True)
+    elif args.batch_config.startswith("streams:"):
+        batch = Batch(plans, sg, sd, outs, streams=int(args.batch_config.split(":", 1)[1]))
     else:
         th, cps, order, spec = args.batch_config.split(",")
         batch = Batch(plans, sg, sd, outs, threads=int(th), ctas_per_sm=int(cps), order=order,
@@ -495,7 +498,11 @@ def run_batch(args):
     model = sum(step_model_bytes(d.nr, d.nphi, 2, 6) for d in discs)
     peak, peak_kind = measured_peaks()
     achieved = model / (ms_graph * 1e-3) / 1e9
-    ratio = batch_profiled_ratio()
+    streams = cfg.get("streams", 0)
+    # the k_batch capture's DRAM ratio describes the persistent engine only
+    ratio = batch_profiled_ratio() if not streams else None
+    engine = (f"every disc's sg_solve launch chain on {streams} forked streams of one CUDA graph per step"
+              if streams else "one persistent launch per step from a CUDA graph")
     from collections import Counter
     shapes = Counter(f"{d.nr}x{d.nphi}" for d in discs)
     result = {"metric": METRIC, "value": cells / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
@@ -503,17 +510,20 @@ def run_batch(args):
               "vs_baseline": None, "dtype": "f32", "data": "synthetic (64 seeded log-normal gas + dust discs)",
               "config": {"workload": f"{len(discs)} independent gas + dust discs, grids drawn from 128x256..1024x2048, "
                                      "h_g in [0.03, 0.1], St in {0.01, 0.1, 1}, outputs Phi + g_r + g_phi "
-                                     "per fluid; one persistent launch per step from a CUDA graph",
+                                     "per fluid; " + engine,
                          "shapes": dict(shapes), "cells": cells,
                          "l2": "flushed between timed steps (256 MiB write)",
                          "kernel_spectra": "built once per plan, outside the timed steps"},
               "batch_config": cfg,
               "autotune_candidates": [dict(c, ms=round(m, 4)) for c, m in tried],
-              "roofline": {"bound": "hbm", "kernel": "k_batch (persistent, whole step)",
+              "roofline": {"bound": "hbm",
+                           "kernel": (f"per-disc solve chains on {streams} streams (whole step)" if streams
+                                      else "k_batch (persistent, whole step)"),
                            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(achieved / peak, 4),
                            "traffic": None if ratio is None else round(ratio * model),
-                           "traffic_note": "DRAM bytes of a 16-disc capture scaled by model bytes",
+                           "traffic_note": ("DRAM bytes of a 16-disc capture scaled by model bytes" if not streams
+                                            else "no capture of the stream engine's whole step"),
                            "peak_source": f"{peak_kind} HBM copy bandwidth",
                            "algorithmic_bytes_per_launch": model},
               "per_disc_loop": {"c_ms_per_step": ms_loop_c, "python_ms_per_step": ms_loop_py,
@@ -521,7 +531,7 @@ def run_batch(args):
                                 "speedup_vs_c_loop": ms_loop_c / ms_graph,
                                 "speedup_vs_python_loop": ms_loop_py / ms_graph},
               "plan_build_ms": build_ms, "autotune_ms": tune_ms,
-              "gpu_launches": K, "clocks": clk}
+              "gpu_launches": K * (cfg["tasks"] if streams else 1), "clocks": clk}
     print(json.dumps(result), flush=True)
     batch.close()
     for p in plans:

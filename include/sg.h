@@ -225,12 +225,14 @@ sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, const void 
  * counter reset and the launch are captured once in a CUDA graph, so
  * sg_batch_solve is one graph launch.
  *
- * Results are those of sg_solve on each plan with the same buffers: the
- * same transforms and products in the same order, bit-identical except that
- * sg_solve's FP32 transforms of length 2048 and 4096 derive 9 of the 15
- * twiddles of each radix-16 pass as products of loaded ones (one extra
- * rounding), where the batch loads all of them.  Results do not depend on
- * the launch configuration (threads, blocks, task order).
+ * A second engine (opts.streams > 0) captures instead, in that one graph,
+ * every disc's sg_solve launch chain on `streams` forked streams (discs
+ * assigned largest first to the least loaded stream), so that the small
+ * discs' kernels overlap the large ones'.  Its results are sg_solve's, bit
+ * for bit.  The persistent engine's results are sg_solve's to FP32 rounding
+ * (its row transforms reduce the row mean and form twiddles in another
+ * order) and do not depend on its launch configuration (threads, blocks,
+ * task order).  With autotune both engines' candidates are timed.
  * ---------------------------------------------------------------------- */
 #define SG_BATCH_HOST_GATE 4u   /* opts flag: blocks wait for sg_batch_release      */
 
@@ -253,6 +255,10 @@ typedef struct {
                               keep the fastest; those four fields are ignored   */
     uint32_t flags;        /* SG_CHECK_FINITE, SG_BATCH_HOST_GATE                   */
     double timeout_ms;     /* bound of each device-side wait (0: 2000 ms)          */
+    int32_t streams;       /* 0: the persistent kernel; 1..64: the per-disc launch
+                              chains on this many streams of one graph (threads,
+                              ctas_per_sm, order, specialize and timeout_ms are
+                              then unused; no SG_BATCH_HOST_GATE)               */
 } sg_batch_opts;
 
 /* Bind `n` FFT plans and their buffers into a batch.  For disc k:
@@ -274,8 +280,8 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n,
                           void *const *outs, const sg_batch_opts *opts, void *stream);
 
 /* Solve every disc of the batch: one graph launch (a 4-byte-per-disc
- * counter reset and the persistent kernel) on `stream`.  Never synchronises
- * the host.  With SG_BATCH_HOST_GATE every block first waits (bounded by
+ * counter reset and the persistent kernel, or the per-disc launch chains on
+ * forked streams) on `stream`.  Never synchronises the host.  With SG_BATCH_HOST_GATE every block first waits (bounded by
  * timeout_ms) until sg_batch_release is called; each gated solve must then
  * be followed by sg_batch_release and sg_batch_sync before the next.      */
 sg_status sg_batch_solve(sg_batch *batch, void *stream);
@@ -295,9 +301,11 @@ sg_status sg_batch_release(sg_batch *batch);
  * flags.                                                                 */
 sg_status sg_batch_sync(sg_batch *batch, void *stream);
 
-/* The configuration in use (threads, ctas_per_sm, order; autotune = 1 if it
- * was tuned), the persistent grid size, the number of tasks and the tuned
- * time per solve in ms (0 when not tuned); any pointer may be NULL.       */
+/* The configuration in use (streams, or threads, ctas_per_sm, order;
+ * autotune = 1 if it was tuned), the persistent grid size (0 for the stream
+ * engine), the number of tasks (kernel launches for the stream engine) and
+ * the tuned time per solve in ms (0 when not tuned); any pointer may be
+ * NULL.                                                                   */
 sg_status sg_batch_config(const sg_batch *batch, sg_batch_opts *opts, int32_t *grid,
                           int32_t *ntasks, float *tuned_ms);
 

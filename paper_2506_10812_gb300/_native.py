@@ -43,7 +43,8 @@ class SgParams(ctypes.Structure):
 
 class SgBatchOpts(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("specialize", ctypes.c_int32), ("autotune", ctypes.c_int32), ("flags", ctypes.c_uint32), ("timeout_ms", ctypes.c_double)]
+                ("specialize", ctypes.c_int32), ("autotune", ctypes.c_int32), ("flags", ctypes.c_uint32), ("timeout_ms", ctypes.c_double),
+                ("streams", ctypes.c_int32)]
 
 
 class SgError(RuntimeError):

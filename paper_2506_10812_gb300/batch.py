@@ -19,11 +19,14 @@ class Batch:
     must stay alive and at the same addresses for the batch's lifetime.
     ``threads`` (256 / 512), ``ctas_per_sm``, ``order`` ("pipelined" /
     "staged") and ``specialize`` (compile-time transforms for the lengths the
-    per-disc path specialises) fix the launch unless ``autotune`` times every
-    candidate and keeps the fastest."""
+    per-disc path specialises) fix the persistent kernel's launch; ``streams``
+    > 0 selects the other engine, every disc's sg_solve chain on that many
+    streams of one graph.  ``autotune`` times every candidate of both engines
+    and keeps the fastest."""
 
     def __init__(self, plans, sigma_g, sigma_d, outs, threads=0, ctas_per_sm=0, order="pipelined",
-                 specialize=False, autotune=False, check_finite=False, host_gate=False, timeout_ms=0.0):
+                 specialize=False, autotune=False, check_finite=False, host_gate=False, timeout_ms=0.0,
+                 streams=0):
         self._lib = N.load()
         n = len(plans)
         if not (len(sigma_g) == len(sigma_d) == len(outs) == n) or n < 1:
@@ -52,6 +55,7 @@ class Batch:
         o.autotune = 1 if autotune else 0
         o.flags = (N.SG_CHECK_FINITE if check_finite else 0) | (N.SG_BATCH_HOST_GATE if host_gate else 0)
         o.timeout_ms = float(timeout_ms)
+        o.streams = int(streams)
         hp = (ctypes.c_void_p * n)(*[pl._h.value for pl in plans])
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -87,7 +91,7 @@ class Batch:
                                           ctypes.byref(ms)), what="sg_batch_config", batch_handle=self._h)
         return {"threads": o.threads, "ctas_per_sm": o.ctas_per_sm,
                 "order": ("pipelined", "staged")[o.order], "specialize": bool(o.specialize),
-                "autotuned": bool(o.autotune),
+                "autotuned": bool(o.autotune), "streams": o.streams,
                 "grid": grid.value, "tasks": ntasks.value, "tuned_ms": ms.value, "timeout_ms": o.timeout_ms}
 
     def tune_results(self):
@@ -96,7 +100,8 @@ class Batch:
         cfgs = (N.SgBatchOpts * max(n, 1))()
         ms = (ctypes.c_float * max(n, 1))()
         self._lib.sg_batch_tune_results(self._h, n, cfgs, ms)
-        return [({"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "order": ("pipelined", "staged")[c.order],
+        return [({"streams": c.streams} if c.streams else
+                 {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "order": ("pipelined", "staged")[c.order],
                   "specialize": bool(c.specialize)}, float(m)) for c, m in zip(cfgs[:n], ms[:n])]
 
     def close(self):

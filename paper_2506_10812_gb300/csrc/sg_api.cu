@@ -216,12 +216,13 @@ uint32_t outmask_of(const sg_plan *pl, void *const outs[6])
 }
 
 template <typename R>
-sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const outs[6], cudaStream_t s)
+sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const outs[6], cudaStream_t s,
+                  unsigned int *sflag, bool check_finite)
 {
     const uint32_t mask = outmask_of(pl, outs);
     if (!mask) return SG_OK;
     const int nr = pl->p.nr, nphi = pl->p.nphi;
-    unsigned int *flag = (pl->p.flags & SG_CHECK_FINITE) ? pl->flag : nullptr;
+    unsigned int *flag = check_finite ? sflag : nullptr;
     cudaError_t e;
     const bool ev = pl->ev[0] != nullptr;
     if (ev) cudaEventRecord(pl->ev[0], s);
@@ -232,12 +233,12 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
     if (pl->p.method == SG_METHOD_FFT) {
         e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row,
                                pl->twp_row, (const R *)pl->rcen, true, s, 0, -1, pl->tm_rows ? &pl->tm_sh : nullptr,
-                               pl->flag);
+                               sflag);
         if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
         if (ev) cudaEventRecord(pl->ev[1], s);
         e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
-                                         pl->flag, s)
-                       : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s,
+                                         sflag, s)
+                       : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, sflag, s,
                                         0, !ev);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
@@ -250,7 +251,7 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
             ++ro.n;
         }
         e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, 0, -1,
-                               pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag, !ev);
+                               pl->tm_rows ? &pl->tm_oh : nullptr, sflag, !ev);
         if (e != cudaSuccess) return cuda_fail(pl, e, "inverse row transform");
         if (ev) cudaEventRecord(pl->ev[3], s);
     } else {
@@ -272,6 +273,16 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
 sg_status solve_any(sg_plan *pl, const void *sg_, const void *sd_, void *const outs[6], void *stream)
 {
     if (!pl) return SG_ERR_ARG;
+    return solve_into(pl, sg_, sd_, outs, (cudaStream_t)stream, pl->flag, (pl->p.flags & SG_CHECK_FINITE) != 0);
+}
+
+}  // namespace
+
+// Declared in sg_internal.h.
+sg_status solve_into(sg_plan *pl, const void *sg_, const void *sd_, void *const outs[6], cudaStream_t s,
+                     unsigned int *sflag, bool check_finite)
+{
+    if (!pl) return SG_ERR_ARG;
     sg_status st = check_device(pl);
     if (st != SG_OK) return st;
     if (!sg_) return fail(pl, SG_ERR_ARG, "sigma_g is NULL");
@@ -281,9 +292,11 @@ sg_status solve_any(sg_plan *pl, const void *sg_, const void *sd_, void *const o
     bool misaligned = ((uintptr_t)sg_ & amask) || (pl->nsrc == 2 && ((uintptr_t)sd_ & amask));
     for (int q = 0; q < 6; ++q) misaligned |= ((uintptr_t)outs[q] & amask) != 0;
     if (misaligned) return fail(pl, SG_ERR_ARG, "device buffers must be aligned to %d bytes", (int)(amask + 1));
-    cudaStream_t s = (cudaStream_t)stream;
-    return pl->f64 ? solve_t<double>(pl, sg_, sd_, outs, s) : solve_t<float>(pl, sg_, sd_, outs, s);
+    return pl->f64 ? solve_t<double>(pl, sg_, sd_, outs, s, sflag, check_finite)
+                   : solve_t<float>(pl, sg_, sd_, outs, s, sflag, check_finite);
 }
+
+namespace {
 
 // Pipelined host-buffer FFT solve: row chunks of the inputs are copied on the
 // plan's copy stream while the previous chunk's row transforms run on `s`;

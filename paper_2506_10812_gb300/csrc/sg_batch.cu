@@ -668,6 +668,8 @@ struct sg_batch {
     unsigned *ctl = nullptr, *flag = nullptr;
     unsigned *gate_h = nullptr, *gate_d = nullptr;
     cudaStream_t cs = nullptr;           // capture stream
+    std::vector<cudaStream_t> ss;        // stream engine: the forked streams
+    std::vector<cudaEvent_t> sev;        // ... and their join events (+ the fork event last)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     char err[256] = {0};
@@ -860,8 +862,90 @@ sg_status configure_k(sg_batch *b, int threads, int ctas_per_sm, int order)
     b->cfg.ctas_per_sm = cps;
     b->cfg.order = order;
     b->cfg.specialize = SPEC ? 1 : 0;
+    b->cfg.streams = 0;
     b->grid = grid;
     b->ntasks = (int)tasks.size();
+    return SG_OK;
+}
+
+// The stream engine: every disc's sg_solve launch chain captured in one graph
+// on K forked streams, discs assigned largest first to the least loaded
+// stream (load = the disc's model traffic in 4-byte units per cell: sources
+// nsrc, row spectra written and read 2 nsrc, kernel spectra nsrc nout,
+// column output written and read 2 nout, outputs nout), status words in
+// b->flag.
+sg_status configure_streams(sg_batch *b, int K)
+{
+    cudaError_t e = cudaSuccess;
+    while ((int)b->ss.size() < K && e == cudaSuccess) {
+        cudaStream_t st = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->ss.push_back(st);
+    }
+    while ((int)b->sev.size() < 65 && e == cudaSuccess) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->sev.push_back(ev);
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "batch streams");
+    std::vector<double> cost(b->n);
+    int launches = 0;
+    for (int k = 0; k < b->n; ++k) {
+        const sg_plan *pl = b->plans[k];
+        const uint32_t m = batch_outmask(b, k);
+        const int nout = __builtin_popcount(m);
+        cost[k] = (double)pl->p.nr * pl->p.nphi * (3 * pl->nsrc + pl->nsrc * nout + 3 * nout);
+        launches += m ? 3 : 0;
+    }
+    std::vector<int> order(b->n);
+    for (int k = 0; k < b->n; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<std::vector<int>> assign(K);
+    std::vector<double> load(K, 0.0);
+    for (int k : order) {
+        const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        assign[j].push_back(k);
+        load[j] += cost[k];
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    const bool finite = (b->flags & SG_CHECK_FINITE) != 0;
+    cudaEvent_t fork = b->sev[64];
+    e = cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bcuda(b, e, "graph capture");
+    sg_status st = SG_OK;
+    e = cudaEventRecord(fork, b->cs);
+    for (int j = 0; j < K && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(b->ss[j], fork, 0);
+    for (int j = 0; j < K && e == cudaSuccess && st == SG_OK; ++j)
+        for (int k : assign[j]) {
+            st = solve_into(b->plans[k], b->sg[k], b->sd[k], b->outs.data() + 6 * (size_t)k, b->ss[j], b->flag,
+                            finite);
+            if (st != SG_OK) {
+                bfail(b, st, "disc %d: %s", k, sg_last_error(b->plans[k]));
+                break;
+            }
+        }
+    for (int j = 0; j < K && e == cudaSuccess; ++j) {
+        e = cudaEventRecord(b->sev[j], b->ss[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cs, b->sev[j], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->cs, &g);
+    if (st != SG_OK || e != cudaSuccess || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (st != SG_OK) return st;
+        return bcuda(b, e != cudaSuccess ? e : ce, "stream-engine capture");
+    }
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) return bcuda(b, e, "graph instantiate");
+    b->cfg.threads = b->cfg.ctas_per_sm = b->cfg.order = b->cfg.specialize = 0;
+    b->cfg.streams = K;
+    b->grid = 0;
+    b->ntasks = launches;
     return SG_OK;
 }
 
@@ -901,7 +985,7 @@ sg_status time_config(sg_batch *b, cudaStream_t s, int reps, float *ms)
     if (e != cudaSuccess) return bcuda(b, e, "autotune run");
     unsigned f = 0;
     cudaMemcpy(&f, b->flag, sizeof(f), cudaMemcpyDeviceToHost);
-    if (f & 4u) return bfail(b, SG_ERR_TIMEOUT, "a device wait gave up while tuning");
+    if (f & 6u) return bfail(b, SG_ERR_TIMEOUT, "a device wait gave up while tuning");
     std::sort(t.begin(), t.end());
     *ms = t[t.size() / 2];
     return SG_OK;
@@ -912,6 +996,8 @@ void batch_free(sg_batch *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cs) cudaStreamDestroy(b->cs);
+    for (cudaStream_t st : b->ss) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->sev) cudaEventDestroy(ev);
     void *ptrs[] = {b->discs, b->tasks, b->ctl, b->flag};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -951,6 +1037,9 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, cons
     if (o.order != SG_BATCH_ORDER_PIPELINED && o.order != SG_BATCH_ORDER_STAGED)
         return reject(SG_ERR_ARG, "unknown order", -1);
     if (!(o.timeout_ms >= 0) || o.timeout_ms > 600000) return reject(SG_ERR_ARG, "timeout_ms out of range", -1);
+    if (o.streams < 0 || o.streams > 64) return reject(SG_ERR_ARG, "streams must be 0..64", -1);
+    if (o.streams > 0 && (o.flags & SG_BATCH_HOST_GATE))
+        return reject(SG_ERR_ARG, "the host gate needs the persistent engine (streams = 0)", -1);
 
     sg_batch *b = new (std::nothrow) sg_batch();
     if (!b) return SG_ERR_OOM;
@@ -1020,11 +1109,31 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, cons
                 }
             }
         }
+        for (int K : {2, 4, 8, 16, 32}) {
+            if (K > 2 * b->n) break;
+            st = configure_streams(b, std::min(K, b->n));
+            if (st != SG_OK) return bad(st);
+            float ms = 0.f;
+            st = time_config(b, (cudaStream_t)stream, 5, &ms);
+            if (st != SG_OK) return bad(st);
+            b->tried.push_back(b->cfg);
+            b->tried_ms.push_back(ms);
+            if (!have || ms < best) {
+                best = ms;
+                bc = b->cfg;
+                have = true;
+            }
+            if (K >= b->n) break;
+        }
         if (!have) return bad(bfail(b, SG_ERR_UNSUPPORTED, "no batch configuration fits (transforms too long)"));
-        st = configure_any(b, bc.threads, bc.ctas_per_sm, bc.order, bc.specialize != 0);
+        st = bc.streams ? configure_streams(b, bc.streams)
+                        : configure_any(b, bc.threads, bc.ctas_per_sm, bc.order, bc.specialize != 0);
         if (st != SG_OK) return bad(st);
         b->cfg.autotune = 1;
         b->tuned_ms = best;
+    } else if (o.streams > 0) {
+        st = configure_streams(b, o.streams);
+        if (st != SG_OK) return bad(st);
     } else {
         const int threads = o.threads ? o.threads : 256;
         if (!threads_fit(b, threads))
@@ -1080,7 +1189,8 @@ sg_status sg_batch_sync(sg_batch *b, void *stream)
     e = cudaMemcpy(&f, b->flag, sizeof(f), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && f) e = cudaMemset(b->flag, 0, sizeof(unsigned));
     if (e != cudaSuccess) return bcuda(b, e, "flag read");
-    if (f & 4u) return bfail(b, SG_ERR_TIMEOUT, "a device-side wait gave up (outputs incomplete)");
+    // bit 4: a wait of the persistent kernel; bit 2: a staged copy of a per-disc chain
+    if (f & 6u) return bfail(b, SG_ERR_TIMEOUT, "a device-side wait gave up (outputs incomplete)");
     if (f & 1u) return bfail(b, SG_ERR_NONFINITE, "non-finite output");
     return SG_OK;
 }

@@ -148,3 +148,9 @@ struct sg_plan {
     CUtensorMap tm_sh{}, tm_oh{};         // the row transforms' views of sh and oh
     char err[256] = {0};
 };
+
+// sg_solve's argument checks and launch chain on `s`, with the status word
+// `sflag` (bit 1: non-finite output when check_finite; bit 2: a staged copy
+// that never completed) in place of the plan's own (sg_api.cu).
+sg_status solve_into(sg_plan *pl, const void *sigma_g, const void *sigma_d, void *const outs[6], cudaStream_t s,
+                     unsigned int *sflag, bool check_finite);

@@ -1,7 +1,9 @@
 """GPU tests of the batched solve (many independent discs, one persistent
-launch under a CUDA graph): against the per-disc solve, against the FP64
-oracle, across launch configurations, with output subsets, and the bounded
-device waits (host gate withheld -> SG_ERR_TIMEOUT, context still usable).
+launch under a CUDA graph, or every disc's launch chain on forked streams of
+one graph): against the per-disc solve, against the FP64 oracle, across
+launch configurations, with output subsets, the autotuner over both engines,
+and the bounded device waits (host gate withheld -> SG_ERR_TIMEOUT, context
+still usable).
 """
 import numpy as np
 import pytest
@@ -147,6 +149,65 @@ def test_launch_configurations_are_bit_identical():
                         for a, c in zip(first, cur):
                             for x in a:
                                 assert torch.equal(a[x], c[x]), (threads, order, cps, x)
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_stream_engine_equals_per_disc_solve(dtype):
+    """The stream engine captures every disc's sg_solve chain on forked
+    streams of one graph: its outputs equal the per-disc solve bit for bit
+    (output subsets, one stream, several, more streams than discs), over
+    repeated solves."""
+    keys = lambda k: KEYS if k % 3 else ("gr_g", "phi_d")
+    S = Setup(uneven(), dtype=dtype, keys=keys)
+    try:
+        ref = S.per_disc()
+        for streams in (1, 3, 16):
+            for o in S.out:
+                for t in o.values():
+                    t.fill_(float("nan"))
+            with S.batch(streams=streams) as b:
+                cfg = b.config()
+                assert cfg["streams"] == streams and cfg["grid"] == 0 and cfg["tasks"] == 3 * len(S.discs)
+                b.solve()
+                b.solve()
+                b.sync()
+            for k in range(len(S.discs)):
+                for x in S.keys[k]:
+                    assert torch.equal(S.out[k][x], ref[k][x]), (streams, k, x)
+    finally:
+        S.close()
+
+
+def test_autotune_times_both_engines():
+    S = Setup(uneven(4, offset=90))
+    try:
+        ref = S.per_disc()
+        with S.batch(autotune=True) as b:
+            tried = b.tune_results()
+            assert any("streams" in c for c, _ in tried) and any("threads" in c for c, _ in tried)
+            cfg = b.config()
+            best = min(ms for _, ms in tried)
+            assert cfg["autotuned"] and cfg["tuned_ms"] == pytest.approx(best)
+            b.solve()
+            b.sync()
+        for k in range(4):
+            for x in S.keys[k]:
+                assert rel(S.out[k][x], ref[k][x]) <= 1e-6, (k, x)
+    finally:
+        S.close()
+
+
+def test_stream_engine_rejects_host_gate():
+    S = Setup(uneven(2))
+    try:
+        with pytest.raises(N.SgError) as e:
+            S.batch(streams=2, host_gate=True)
+        assert e.value.status == N.SG_ERR_ARG
+        with pytest.raises(N.SgError) as e:
+            S.batch(streams=65)
+        assert e.value.status == N.SG_ERR_ARG
     finally:
         S.close()
 
