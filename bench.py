@@ -36,6 +36,7 @@ UNIT = "cells/s"
 L2_FLUSH_BYTES = 256 << 20
 PROFILE = os.path.join(ROOT, "profiles", "cols_2048x4096.md")
 BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_64discs.md")
+BATCH_STREAMS_PROFILE = os.path.join(ROOT, "profiles", "batch_streams_64discs.md")
 
 
 def parse():
@@ -186,16 +187,19 @@ def profiled_traffic():
     return float(t.group(1))
 
 
-def batch_profiled_ratio():
-    """DRAM bytes per model byte of the persistent batch kernel, from the
-    committed ncu summary of a smaller batch (same kernel source)."""
+def batch_profiled_ratio(streams=False):
+    """DRAM bytes per model byte of a batch step, from the committed ncu
+    summary of a smaller batch on the same sources: the persistent kernel's,
+    or (streams) the sum over the per-disc launch chains of one step."""
+    path, names = ((BATCH_STREAMS_PROFILE, ("sg_batch.cu", "sg_kernels.cu", "sg_fft.cuh", "sg_mem.cuh")) if streams
+                   else (BATCH_PROFILE, ("sg_batch.cu", "sg_fft.cuh", "sg_mem.cuh")))
     try:
-        txt = open(BATCH_PROFILE).read()
+        txt = open(path).read()
     except OSError:
         return None
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_model_byte:\s*([0-9.eE+]+)", txt)
-    if not (m and t) or m.group(1) != kernel_source_hash(("sg_batch.cu", "sg_fft.cuh", "sg_mem.cuh")):
+    if not (m and t) or m.group(1) != kernel_source_hash(names):
         return None
     return float(t.group(1))
 
@@ -499,8 +503,7 @@ def run_batch(args):
     peak, peak_kind = measured_peaks()
     achieved = model / (ms_graph * 1e-3) / 1e9
     streams = cfg.get("streams", 0)
-    # the k_batch capture's DRAM ratio describes the persistent engine only
-    ratio = batch_profiled_ratio() if not streams else None
+    ratio = batch_profiled_ratio(streams=bool(streams))
     engine = (f"every disc's sg_solve launch chain on {streams} forked streams of one CUDA graph per step"
               if streams else "one persistent launch per step from a CUDA graph")
     from collections import Counter
@@ -522,8 +525,9 @@ def run_batch(args):
                            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                            "frac": round(achieved / peak, 4),
                            "traffic": None if ratio is None else round(ratio * model),
-                           "traffic_note": ("DRAM bytes of a 16-disc capture scaled by model bytes" if not streams
-                                            else "no capture of the stream engine's whole step"),
+                           "traffic_note": "DRAM bytes of a 16-disc capture scaled by model bytes"
+                                           + (" (sum over one step's launches, each on a flushed cache)"
+                                              if streams else ""),
                            "peak_source": f"{peak_kind} HBM copy bandwidth",
                            "algorithmic_bytes_per_launch": model},
               "per_disc_loop": {"c_ms_per_step": ms_loop_c, "python_ms_per_step": ms_loop_py,
