@@ -204,7 +204,7 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 }
 
 // ------------------------------------------- tensor-copy row transforms
-// FP32 row transforms of the hot lengths (nphi = 2 NC, NC = 1024 or 2048),
+// FP32 row transforms of the compiled lengths (nphi = 2 NC, NC = 256 .. 2048),
 // four rows per CTA, whose [N][rows] side moves by 2-D tensor copies: the
 // forward transform leaves its [N][4] spectrum tile with bulk tensor stores,
 // the inverse transform receives its tile by bulk tensor loads, so neither
@@ -270,10 +270,10 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
                int dc, unsigned int *tflag, int row0)
 {
     constexpr int N = NC, T = N / 16, NW = T / 8, PLS = row_pitch_tma(N), XS = T + T / 16;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_tma[];
     griddep_launch();                     // the column pass may set up once every row CTA runs
-    float *red = reinterpret_cast<float *>(smem_raw + 64);              // NW x 4 partial sums
-    float2 *reg = reinterpret_cast<float2 *>(smem_raw + kRowHdr);
+    float *red = reinterpret_cast<float *>(smem_tma + 64);              // NW x 4 partial sums
+    float2 *reg = reinterpret_cast<float2 *>(smem_tma + kRowHdr);
     if (smem_u32(reg) & 127u) {                                         // TMA alignment (never expected)
         if (threadIdx.x == 0 && tflag) atomicOr(tflag, 2u);
         return;
@@ -289,7 +289,7 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
         // keeps the 4-row x 4-column half-warp reads conflict-free; the
         // staging overlays the exchange buffers (the transform synchronises first)
         constexpr int IPS = N + 4;
-        uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem_tma);
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -486,7 +486,9 @@ cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nr
                                                                row0);
             };
             if (nphi == 4096) go(k_rows_fwd_tma<2048>, 2048);
-            else go(k_rows_fwd_tma<1024>, 1024);
+            else if (nphi == 2048) go(k_rows_fwd_tma<1024>, 1024);
+            else if (nphi == 1024) go(k_rows_fwd_tma<512>, 512);
+            else go(k_rows_fwd_tma<256>, 256);
             return cudaGetLastError();
         }
     }
@@ -824,10 +826,16 @@ cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int n
     if (nsrc == 1) {
         if (!f64 && L == 4096) go(k_cols<R, 1, 4096>);
         else if (!f64 && L == 2048) go(k_cols<R, 1, 2048>);
+        else if (!f64 && L == 1024) go(k_cols<R, 1, 1024>);
+        else if (!f64 && L == 512) go(k_cols<R, 1, 512>);
+        else if (!f64 && L == 256) go(k_cols<R, 1, 256>);
         else go(k_cols<R, 1, 0>);
     } else {
         if (!f64 && L == 4096) go(k_cols<R, 2, 4096>);
         else if (!f64 && L == 2048) go(k_cols<R, 2, 2048>);
+        else if (!f64 && L == 1024) go(k_cols<R, 2, 1024>);
+        else if (!f64 && L == 512) go(k_cols<R, 2, 512>);
+        else if (!f64 && L == 256) go(k_cols<R, 2, 256>);
         else go(k_cols<R, 2, 0>);
     }
     return err != cudaSuccess ? err : cudaGetLastError();
@@ -988,9 +996,9 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
                unsigned int *tflag, int row0)
 {
     constexpr int N = NC, T = N / 16, PLS = row_pitch_tma(N);
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-    float2 *reg = reinterpret_cast<float2 *>(smem_raw + kRowHdr);
+    extern __shared__ __align__(1024) unsigned char smem_tma[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_tma);
+    float2 *reg = reinterpret_cast<float2 *>(smem_tma + kRowHdr);
     if (smem_u32(reg) & 127u) {                                         // TMA alignment (never expected)
         if (threadIdx.x == 0 && tflag) atomicOr(tflag, 2u);
         return;
@@ -1073,7 +1081,8 @@ cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols)
 
 bool rows_tma_eligible(int nr, int nphi, bool f64)
 {
-    return !f64 && BW == 1 && (nphi == 2048 || nphi == 4096) && nr % 4 == 0 && row_rpc(nphi, false) == 4;
+    return !f64 && BW == 1 && (nphi == 512 || nphi == 1024 || nphi == 2048 || nphi == 4096) && nr % 4 == 0 &&
+           row_rpc(nphi, false) == 4;
 }
 
 template <typename R>
@@ -1093,7 +1102,9 @@ cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, c
                                 (const float2 *)tw_row, (const float2 *)twp_row, rcen, flag, tflag, row0);
             };
             if (nphi == 4096) go(k_rows_inv_tma<2048>, 2048);
-            else go(k_rows_inv_tma<1024>, 1024);
+            else if (nphi == 2048) go(k_rows_inv_tma<1024>, 1024);
+            else if (nphi == 1024) go(k_rows_inv_tma<512>, 512);
+            else go(k_rows_inv_tma<256>, 256);
             return err != cudaSuccess ? err : cudaGetLastError();
         }
     }
@@ -1123,7 +1134,12 @@ cudaError_t set_smem_limits(int max_optin)
                          (const void *)k_cols<double, 1, 0>,      (const void *)k_cols<double, 2, 0>,
                          (const void *)k_tabcols<float>,          (const void *)k_tabcols<double>,
                          (const void *)k_rows_fwd_tma<2048>,      (const void *)k_rows_fwd_tma<1024>,
-                         (const void *)k_rows_inv_tma<2048>,      (const void *)k_rows_inv_tma<1024>};
+                         (const void *)k_rows_inv_tma<2048>,      (const void *)k_rows_inv_tma<1024>,
+                         (const void *)k_rows_fwd_tma<512>,       (const void *)k_rows_fwd_tma<256>,
+                         (const void *)k_rows_inv_tma<512>,       (const void *)k_rows_inv_tma<256>,
+                         (const void *)k_cols<float, 1, 1024>,    (const void *)k_cols<float, 1, 512>,
+                         (const void *)k_cols<float, 1, 256>,     (const void *)k_cols<float, 2, 1024>,
+                         (const void *)k_cols<float, 2, 512>,     (const void *)k_cols<float, 2, 256>};
     for (const void *fn : fns) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
         if (e != cudaSuccess) return e;

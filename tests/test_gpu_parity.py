@@ -153,6 +153,17 @@ def test_fft_edge_sizes(nr, nphi, bif, dtype):
     assert_close(gpu_solve(d, dtype), ref, tol, f"{nr}x{nphi}")
 
 
+@pytest.mark.parametrize("nr,nphi,bif", [
+    (128, 512, False), (256, 1024, False), (512, 512, False),   # gas: columns 256 / 512 / 1024, rows 512 / 1024
+    (128, 1024, True), (256, 512, True), (512, 1024, True)])    # gas + dust, the same lengths
+def test_compiled_small_lengths(nr, nphi, bif):
+    """Columns of 256, 512 and 1024 and tensor-copy rows of 512 and 1024 run
+    compile-time kernels: FP32 tolerance against the FP64 oracle."""
+    d = rounded(inputs.ragged_noise(nr, nphi, bifluid=bif, offset=61 + nr), torch.float32)
+    ref = oracle.fft64(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G)
+    assert_close(gpu_solve(d), ref, TOL32, f"{nr}x{nphi}")
+
+
 # ----------------------------------------------------------- full sizes
 @pytest.mark.parametrize("nr,nphi", [(1024, 2048), (2048, 4096)])
 def test_lognormal_full_size(nr, nphi):
