@@ -460,8 +460,10 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
         SG_TRY(cudaMalloc(&pl->sh, (size_t)pl->nsrc * pl->N * p->nr * cbytes), "scratch");
         SG_TRY(cudaMalloc(&pl->oh, (size_t)pl->nsrc * 3 * pl->N * p->nr * cbytes), "scratch");
         if (rows_tma_eligible(p->nr, p->nphi, pl->f64))
-            pl->tm_rows = encode_row_map(&pl->tm_sh, pl->sh, p->nr, (long long)pl->nsrc * pl->N) == cudaSuccess &&
-                          encode_row_map(&pl->tm_oh, pl->oh, p->nr, (long long)pl->nsrc * 3 * pl->N) == cudaSuccess;
+            pl->tm_rows = encode_row_map(&pl->tm_sh, pl->sh, p->nr, (long long)pl->nsrc * pl->N,
+                                         rows_tma_fwd_rows()) == cudaSuccess &&
+                          encode_row_map(&pl->tm_oh, pl->oh, p->nr, (long long)pl->nsrc * 3 * pl->N,
+                                         rows_tma_inv_rows()) == cudaSuccess;
         sg_status st = build_tables(pl, s);
         if (st != SG_OK) {
             fprintf(stderr, "sg_plan_create: %s\n", pl->err);

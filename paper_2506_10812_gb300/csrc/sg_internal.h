@@ -53,8 +53,12 @@ cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nr
 
 // 2-D tensor map of a [ncols][nr] complex FP32 intermediate for the
 // tensor-copy row transforms; rows_tma_eligible: the sizes they take.
-cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols);
+// `rows`: rows per CTA of the kernel that uses the map (rows_tma_fwd_rows for
+// the row spectra, rows_tma_inv_rows for the column output).
+cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols, int rows);
 bool rows_tma_eligible(int nr, int nphi, bool f64);
+int rows_tma_fwd_rows();
+int rows_tma_inv_rows();
 
 // Column pass of the solve: forward padded FFT of every source column,
 // products with the packed kernel spectra, inverse FFT of every requested

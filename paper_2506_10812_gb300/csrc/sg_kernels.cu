@@ -205,17 +205,15 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 
 // ------------------------------------------- tensor-copy row transforms
 // FP32 row transforms of the compiled lengths (nphi = 2 NC, NC = 256 .. 2048),
-// four rows per CTA, whose [N][rows] side moves by 2-D tensor copies: the
-// forward transform leaves its [N][4] spectrum tile with bulk tensor stores,
-// the inverse transform receives its tile by bulk tensor loads, so neither
-// spends load/store-unit instructions on the 32-byte column slices.  The
-// tile is dense, (k, g) at 4 k + g; lane l of warp w owns row g = l & 3 and
-// transform thread t = 8 w + (l >> 2), so each half-warp (the unit in which
-// shared memory serves 8-byte accesses) touches 16 consecutive tile slots.
-// Row g's exchange buffer starts at g * row_pitch_tma(N) elements, a pitch
-// = 4 (mod 16): a half-warp's 4 rows x 4 consecutive indices then fall in 16
-// distinct bank pairs in every transform exchange.
-// The forward kernel also stages its four input rows by 1-D bulk copies (so
+// NR rows per CTA, whose [N][rows] side moves by 2-D tensor
+// copies: the forward transform leaves its [N][NR] spectrum tile with bulk
+// tensor stores, the inverse transform receives its tile by bulk tensor
+// loads, so neither spends load/store-unit instructions on the column slices.
+// The tile is dense, (k, g) at NR k + g; lane l of warp w owns row g = l mod
+// NR and transform thread t = w 32 / NR + l / NR, so each half-warp (the unit
+// in which shared memory serves 8-byte accesses) touches 16 consecutive tile
+// slots.  Row g's exchange buffer starts at g * row_pitch_tma(N) elements.
+// The forward kernel also stages its input rows by 1-D bulk copies (so
 // it needs 16-byte aligned inputs; the launch falls back to the transpose
 // kernel otherwise).  On the 2048 x 4096 disc the pair takes 28.0 + 52.5 us
 // per solve against 30.5 + 64.0 us for the load/store-unit transpose
@@ -223,13 +221,32 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 #ifndef SG_ROWS_FWD_TMA
 #define SG_ROWS_FWD_TMA 1          // 0: forward rows by the load/store-unit transpose kernel
 #endif
+// Rows per CTA: 4 for the forward transform, 2 for the inverse (2048 x 4096
+// disc: the inverse 51.0 -> 45.3 us with 2, the forward 27.2 -> 30.6 us; a
+// shared-memory floor holding the 2-row inverse to 3 CTAs per SM, 49.0 us).
+#ifndef SG_ROWS_FWD_NR
+#define SG_ROWS_FWD_NR 4
+#endif
+#ifndef SG_ROWS_INV_NR
+#define SG_ROWS_INV_NR 2
+#endif
+constexpr int kRowsFwdNR = SG_ROWS_FWD_NR, kRowsInvNR = SG_ROWS_INV_NR;
+static_assert((kRowsFwdNR == 2 || kRowsFwdNR == 4) && (kRowsInvNR == 2 || kRowsInvNR == 4),
+              "the tensor-copy row transforms take 2 or 4 rows per CTA");
 constexpr int kRowHdr = 1024;                     // mbarrier + partial sums; the tile starts 1024-aligned
-__host__ __device__ constexpr int row_pitch_tma(int N) { return padded_len(N) + 3; }
-size_t row_tma_smem_bytes(int N)
+// row pitch = 16 / NR (mod 16): a half-warp's NR rows x 16 / NR consecutive
+// indices fall in 16 distinct bank pairs
+__host__ __device__ constexpr int row_pitch_tma(int N, int NR) { return padded_len(N) + 16 / NR - 1; }
+// threads of an NR-row CTA of length-2 NC rows, and the CTAs per SM at 64 registers
+constexpr int rows_tma_threads(int NC, int NR) { return NR * NC / 16; }
+constexpr int rows_tma_min_blocks(int NC, int NR) { return 1024 / rows_tma_threads(NC, NR); }
+size_t row_tma_smem_bytes(int N, int NR)
 {
-    const size_t tile = (size_t)N * 4 * 8, xb = (size_t)4 * row_pitch_tma(N) * 8;
+    const size_t tile = (size_t)N * NR * 8, xb = (size_t)NR * row_pitch_tma(N, NR) * 8;
     return kRowHdr + (tile > xb ? tile : xb);
 }
+int rows_tma_fwd_rows() { return kRowsFwdNR; }
+int rows_tma_inv_rows() { return kRowsInvNR; }
 
 // cos(2 pi e / 32), e = 0..8
 __device__ constexpr double kCos32[9] = {1.0,
@@ -264,39 +281,39 @@ template <int E, typename F> __device__ __forceinline__ void unroll16(F &&f)
 }
 
 template <int NC>
-__global__ void __launch_bounds__(NC / 4, 4096 / NC)
+__global__ void __launch_bounds__(rows_tma_threads(NC, kRowsFwdNR), rows_tma_min_blocks(NC, kRowsFwdNR))
 k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const __grid_constant__ CUtensorMap tm,
                const float2 *__restrict__ tw, const float2 *__restrict__ twp, const float *__restrict__ rscale,
                int dc, unsigned int *tflag, int row0)
 {
-    constexpr int N = NC, T = N / 16, NW = T / 8, PLS = row_pitch_tma(N), XS = T + T / 16;
+    constexpr int NR = kRowsFwdNR, N = NC, T = N / 16, NW = NR * T / 32, PLS = row_pitch_tma(N, NR), XS = T + T / 16;
     extern __shared__ __align__(1024) unsigned char smem_tma[];
     griddep_launch();                     // the column pass may set up once every row CTA runs
-    float *red = reinterpret_cast<float *>(smem_tma + 64);              // NW x 4 partial sums
+    float *red = reinterpret_cast<float *>(smem_tma + 64);              // NW x NR partial sums
     float2 *reg = reinterpret_cast<float2 *>(smem_tma + kRowHdr);
     if (smem_u32(reg) & 127u) {                                         // TMA alignment (never expected)
         if (threadIdx.x == 0 && tflag) atomicOr(tflag, 2u);
         return;
     }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane & 3, t = (w << 3) | (lane >> 2);
-    const int a = blockIdx.y, i0 = row0 + blockIdx.x * 4, i = i0 + g;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane & (NR - 1), t = w * (32 / NR) + lane / NR;
+    const int a = blockIdx.y, i0 = row0 + blockIdx.x * NR, i = i0 + g;
     const float *xa = a == 0 ? x0 : x1;
     const float sc = rscale ? rscale[i] : 1.f;
     const float2 w0 = __ldg(&tw[t]);                     // R2C twiddle base, used after the transform
     float2 v[16];
     {
-        // the four rows (contiguous) land at a pitch of N + 4 complex, which
-        // keeps the 4-row x 4-column half-warp reads conflict-free; the
-        // staging overlays the exchange buffers (the transform synchronises first)
-        constexpr int IPS = N + 4;
+        // the NR rows (contiguous) land at a pitch of N + 16 / NR complex,
+        // which keeps the half-warp reads conflict-free; the staging overlays
+        // the exchange buffers (the transform synchronises first)
+        constexpr int IPS = N + 16 / NR;
         uint64_t *bar = reinterpret_cast<uint64_t *>(smem_tma);
         if (threadIdx.x == 0) mbar_init(bar, 1);
         __syncthreads();
         if (threadIdx.x == 0) {
             const uint64_t pf = l2_evict_first();
-            mbar_expect_tx(bar, (unsigned)N * 32u);
+            mbar_expect_tx(bar, (unsigned)N * 8u * NR);
 #pragma unroll
-            for (int r = 0; r < 4; ++r) tma_load_1d(reg + r * IPS, xa + (size_t)(i0 + r) * 2 * N, N * 8, bar, pf);
+            for (int r = 0; r < NR; ++r) tma_load_1d(reg + r * IPS, xa + (size_t)(i0 + r) * 2 * N, N * 8, bar, pf);
         }
         if (!__syncthreads_and(mbar_wait_bounded(bar, 0, tflag))) return;
         const float2 *xs = reg + g * IPS + t;
@@ -311,15 +328,14 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
         float s = 0.f;
 #pragma unroll
         for (int e = 0; e < 16; ++e) s += v[e].x + v[e].y;
-        // lanes of one row differ in bits 2..4
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        s += __shfl_xor_sync(0xffffffffu, s, 8);
-        s += __shfl_xor_sync(0xffffffffu, s, 16);
-        if (lane < 4) red[w * 4 + lane] = s;
+        // lanes of one row differ in the bits above log2(NR)
+#pragma unroll
+        for (int m = NR; m < 32; m <<= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+        if (lane < NR) red[w * NR + lane] = s;
         __syncthreads();
         s = 0.f;
 #pragma unroll
-        for (int ww = 0; ww < NW; ++ww) s += red[ww * 4 + g];
+        for (int ww = 0; ww < NW; ++ww) s += red[ww * NR + g];
         mean = s / (float)(2 * N);
 #pragma unroll
         for (int e = 0; e < 16; ++e) v[e] = make_float2(v[e].x - mean, v[e].y - mean);
@@ -347,15 +363,15 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
         }
     });
     __syncthreads();                                      // the tile overwrites the exchange buffers
-    float2 *tl = reg + 4 * t + g;
+    float2 *tl = reg + NR * t + g;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) tl[4 * T * e] = v[e];
+    for (int e = 0; e < 16; ++e) tl[NR * T * e] = v[e];
     fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint64_t pl = l2_evict_last();
 #pragma unroll
-        for (int b = 0; b < N / 256; ++b) tma_store_2d(&tm, 2 * i0, a * N + 256 * b, reg + 4 * 256 * b, pl);
+        for (int b = 0; b < N / 256; ++b) tma_store_2d(&tm, 2 * i0, a * N + 256 * b, reg + NR * 256 * b, pl);
         bulk_commit();
         bulk_wait_read_all();
     }
@@ -480,8 +496,9 @@ cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nr
     if constexpr (sizeof(R) == 4 && SG_ROWS_FWD_TMA) {
         const bool aligned = ((uintptr_t)x0 & 15u) == 0 && ((uintptr_t)x1 & 15u) == 0;
         if (tm && aligned && rows_tma_eligible(nrows, nphi, false)) {
+            const dim3 gt(nrows_run / kRowsFwdNR, nsrc);
             auto go = [&](auto kern, int N) {
-                kern<<<grid, N / 4, row_tma_smem_bytes(N), s>>>(x0, x1, *tm, (const float2 *)tw_row,
+                kern<<<gt, kRowsFwdNR * N / 16, row_tma_smem_bytes(N, kRowsFwdNR), s>>>(x0, x1, *tm, (const float2 *)tw_row,
                                                                (const float2 *)twp_row, rscale, dc ? 1 : 0, tflag,
                                                                row0);
             };
@@ -990,12 +1007,12 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
 }
 
 template <int NC>
-__global__ void __launch_bounds__(NC / 4, 4096 / NC)
+__global__ void __launch_bounds__(rows_tma_threads(NC, kRowsInvNR), rows_tma_min_blocks(NC, kRowsInvNR))
 k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ RowOut o, const float2 *__restrict__ tw,
                const float2 *__restrict__ twp, const float *__restrict__ rcen, unsigned int *flag,
                unsigned int *tflag, int row0)
 {
-    constexpr int N = NC, T = N / 16, PLS = row_pitch_tma(N);
+    constexpr int NR = kRowsInvNR, N = NC, T = N / 16, PLS = row_pitch_tma(N, NR);
     extern __shared__ __align__(1024) unsigned char smem_tma[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_tma);
     float2 *reg = reinterpret_cast<float2 *>(smem_tma + kRowHdr);
@@ -1003,8 +1020,8 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
         if (threadIdx.x == 0 && tflag) atomicOr(tflag, 2u);
         return;
     }
-    const int q = blockIdx.y, i0 = row0 + blockIdx.x * 4;
-    const int lane = threadIdx.x & 31, g = lane & 3, t = ((threadIdx.x >> 5) << 3) | (lane >> 2);
+    const int q = blockIdx.y, i0 = row0 + blockIdx.x * NR;
+    const int lane = threadIdx.x & 31, g = lane & (NR - 1), t = (threadIdx.x >> 5) * (32 / NR) + lane / NR;
     // plan constants, loaded while the tile is in flight
     const float2 w0 = __ldg(&tw[t]);
     const float sc = o.is_phi[q] ? 1.f : 1.f / __ldg(&rcen[i0 + g]);
@@ -1014,21 +1031,21 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
     if (threadIdx.x == 0) {
         // the column pass's output is read for the last time
         const uint64_t pf = l2_evict_first();
-        mbar_expect_tx(bar, (unsigned)N * 32u);
+        mbar_expect_tx(bar, (unsigned)N * 8u * NR);
 #pragma unroll
-        for (int b = 0; b < N / 256; ++b) tma_load_2d(reg + 4 * 256 * b, &tm, 2 * i0, o.src[q] * N + 256 * b, bar, pf);
+        for (int b = 0; b < N / 256; ++b) tma_load_2d(reg + NR * 256 * b, &tm, 2 * i0, o.src[q] * N + 256 * b, bar, pf);
     }
     if (!__syncthreads_and(mbar_wait_bounded(bar, 0, tflag))) return;
     // Z'[k] = (X[k] + X*[N-k]) + i (X[k] - X*[N-k]) W^-k  (= 2 Z[k])
-    const float2 *xa = reg + 4 * t + g, *xc = reg + 4 * (N - t) + g;
+    const float2 *xa = reg + NR * t + g, *xc = reg + NR * (N - t) + g;
     float2 v[16];
     unroll16<0>([&](auto ec) {
         constexpr int e = decltype(ec)::value;
-        const float2 X = xa[4 * T * e];
+        const float2 X = xa[NR * T * e];
         if (e == 0 && t == 0) {
             v[e] = make_float2(X.x + X.y, X.x - X.y);
         } else {
-            const float2 Xc = cconj(xc[-4 * T * e]);
+            const float2 Xc = cconj(xc[-NR * T * e]);
             v[e] = cadd(cadd(X, Xc), cmul_i(cmulc(csub(X, Xc), tw_step<e>(w0))));
         }
     });
@@ -1051,10 +1068,10 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
 }
 
 // Tensor map of a [ncols][nr] complex FP32 intermediate (element (m, i) at
-// m nr + i) as a 2-D FP32 array [ncols][2 nr], box 8 x 256: four rows of 256
-// columns.  The driver's encoder is reached through the runtime's entry-point
+// m nr + i) as a 2-D FP32 array [ncols][2 nr], box 2 rows x 256: a row
+// transform CTA's `rows` rows of 256 columns.  The driver's encoder is reached through the runtime's entry-point
 // query, so the library needs no link against the driver library.
-cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols)
+cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols, int rows)
 {
     using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -1072,7 +1089,7 @@ cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols)
     if (!fn) return cudaErrorNotSupported;
     const cuuint64_t dims[2] = {(cuuint64_t)2 * nr, (cuuint64_t)ncols};
     const cuuint64_t strides[1] = {(cuuint64_t)nr * 8};
-    const cuuint32_t box[2] = {8, 256}, es[2] = {1, 1};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * rows), 256}, es[2] = {1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1081,8 +1098,7 @@ cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols)
 
 bool rows_tma_eligible(int nr, int nphi, bool f64)
 {
-    return !f64 && BW == 1 && (nphi == 512 || nphi == 1024 || nphi == 2048 || nphi == 4096) && nr % 4 == 0 &&
-           row_rpc(nphi, false) == 4;
+    return !f64 && BW == 1 && (nphi == 512 || nphi == 1024 || nphi == 2048 || nphi == 4096) && nr % 4 == 0;
 }
 
 template <typename R>
@@ -1097,8 +1113,9 @@ cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, c
     dim3 grid(nrows_run / rpc, o.n);
     if constexpr (sizeof(R) == 4) {
         if (tm && rows_tma_eligible(nr, nphi, false)) {
+            const dim3 gt(nrows_run / kRowsInvNR, o.n);
             auto go = [&](auto kern, int N) {
-                err = launch_ex(kern, grid, dim3(N / 4), row_tma_smem_bytes(N), s, pdl, *tm, o,
+                err = launch_ex(kern, gt, dim3(kRowsInvNR * N / 16), row_tma_smem_bytes(N, kRowsInvNR), s, pdl, *tm, o,
                                 (const float2 *)tw_row, (const float2 *)twp_row, rcen, flag, tflag, row0);
             };
             if (nphi == 4096) go(k_rows_inv_tma<2048>, 2048);
