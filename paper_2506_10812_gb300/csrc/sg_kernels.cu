@@ -237,9 +237,18 @@ constexpr int kRowHdr = 1024;                     // mbarrier + partial sums; th
 // row pitch = 16 / NR (mod 16): a half-warp's NR rows x 16 / NR consecutive
 // indices fall in 16 distinct bank pairs
 __host__ __device__ constexpr int row_pitch_tma(int N, int NR) { return padded_len(N) + 16 / NR - 1; }
-// threads of an NR-row CTA of length-2 NC rows, and the CTAs per SM at 64 registers
+// The 2-row inverse fits 48 registers without spills at 1280 threads per SM
+// (5 CTAs): 46.9 -> 45.4 us; at 1536 (40 registers) it spills and takes 56 us.
+#ifndef SG_ROWS_INV_SM_THREADS
+#define SG_ROWS_INV_SM_THREADS 1280  // resident threads per SM the inverse kernel is compiled for
+#endif
+// threads of an NR-row CTA of length-2 NC rows, and the CTAs per SM that keep
+// `sm_threads` threads resident (1024: 64 registers each)
 constexpr int rows_tma_threads(int NC, int NR) { return NR * NC / 16; }
-constexpr int rows_tma_min_blocks(int NC, int NR) { return 1024 / rows_tma_threads(NC, NR); }
+constexpr int rows_tma_min_blocks(int NC, int NR, int sm_threads)
+{
+    return sm_threads / rows_tma_threads(NC, NR) < 32 ? sm_threads / rows_tma_threads(NC, NR) : 32;
+}
 size_t row_tma_smem_bytes(int N, int NR)
 {
     const size_t tile = (size_t)N * NR * 8, xb = (size_t)NR * row_pitch_tma(N, NR) * 8;
@@ -281,7 +290,7 @@ template <int E, typename F> __device__ __forceinline__ void unroll16(F &&f)
 }
 
 template <int NC>
-__global__ void __launch_bounds__(rows_tma_threads(NC, kRowsFwdNR), rows_tma_min_blocks(NC, kRowsFwdNR))
+__global__ void __launch_bounds__(rows_tma_threads(NC, kRowsFwdNR), rows_tma_min_blocks(NC, kRowsFwdNR, 1024))
 k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const __grid_constant__ CUtensorMap tm,
                const float2 *__restrict__ tw, const float2 *__restrict__ twp, const float *__restrict__ rscale,
                int dc, unsigned int *tflag, int row0)
@@ -1007,7 +1016,8 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
 }
 
 template <int NC>
-__global__ void __launch_bounds__(rows_tma_threads(NC, kRowsInvNR), rows_tma_min_blocks(NC, kRowsInvNR))
+__global__ void __launch_bounds__(rows_tma_threads(NC, kRowsInvNR),
+                                  rows_tma_min_blocks(NC, kRowsInvNR, SG_ROWS_INV_SM_THREADS))
 k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ RowOut o, const float2 *__restrict__ tw,
                const float2 *__restrict__ twp, const float *__restrict__ rcen, unsigned int *flag,
                unsigned int *tflag, int row0)
