@@ -273,7 +273,8 @@ typedef struct {
  * With opts->autotune the call runs the batch several times on `stream`
  * (outputs are overwritten).  Synchronises `stream`.  Errors: SG_ERR_ARG
  * (NULL, n < 1, mixed dtypes or devices, a direct-method plan, missing
- * sigma_d), SG_ERR_UNSUPPORTED (a transform longer than 16 x threads:
+ * sigma_d, a buffer not aligned to two elements), SG_ERR_UNSUPPORTED (a
+ * transform longer than 16 x threads:
  * nphi > 8192 or nr > 2048 with 256 threads), SG_ERR_OOM, SG_ERR_CUDA.    */
 sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n,
                           const void *const *sigma_g, const void *const *sigma_d,

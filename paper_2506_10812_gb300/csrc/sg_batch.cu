@@ -1032,6 +1032,11 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, cons
         if (pl->nsrc == 1)
             for (int q = 3; q < 6; ++q)
                 if (outs[6 * (size_t)k + q]) return reject(SG_ERR_ARG, "dust output of a gas-only plan", k);
+        // the transforms move element pairs: every buffer aligned to two elements
+        const uintptr_t amask = 2 * pl->esz - 1;
+        bool mis = ((uintptr_t)sigma_g[k] & amask) || (pl->nsrc == 2 && ((uintptr_t)sigma_d[k] & amask));
+        for (int q = 0; q < 6; ++q) mis |= ((uintptr_t)outs[6 * (size_t)k + q] & amask) != 0;
+        if (mis) return reject(SG_ERR_ARG, "a buffer is not aligned to two elements", k);
     }
     if (o.threads != 0 && o.threads != 256 && o.threads != 512) return reject(SG_ERR_ARG, "threads must be 256 or 512", -1);
     if (o.order != SG_BATCH_ORDER_PIPELINED && o.order != SG_BATCH_ORDER_STAGED)

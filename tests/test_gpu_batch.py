@@ -212,6 +212,43 @@ def test_stream_engine_rejects_host_gate():
         S.close()
 
 
+@pytest.mark.parametrize("streams", [0, 2])
+def test_batch_rejects_misaligned_buffers(streams):
+    """Both engines move element pairs: a buffer aligned to one element only
+    is rejected at create (SG_ERR_ARG), before anything is launched."""
+    S = Setup(uneven(2))
+    try:
+        d = S.discs[1]
+        base = torch.zeros(d.nr * d.nphi + 2, device="cuda:0")
+        S.out[1]["gr_g"] = base[1:1 + d.nr * d.nphi].view(d.nr, d.nphi)
+        with pytest.raises(N.SgError) as e:
+            S.batch(streams=streams)
+        assert e.value.status == N.SG_ERR_ARG
+    finally:
+        S.close()
+
+
+def test_stream_engine_reports_nonfinite_outputs():
+    """The stream engine's per-disc chains write their status into the
+    batch's flag: a NaN input gives SG_ERR_NONFINITE at sg_batch_sync, and
+    the flag is cleared for the next solve."""
+    S = Setup(uneven(3, offset=70))
+    try:
+        with S.batch(streams=2, check_finite=True) as b:
+            b.solve()
+            b.sync()
+            S.sg[1][3, 5] = float("nan")
+            b.solve()
+            with pytest.raises(N.SgError) as e:
+                b.sync()
+            assert e.value.status == N.SG_ERR_NONFINITE
+            S.sg[1][3, 5] = 1.0
+            b.solve()
+            b.sync()
+    finally:
+        S.close()
+
+
 def test_specialized_transforms():
     """The length-specialised kernel: within FP32 rounding of sg_solve and of
     the generic batch (sg_solve's tensor-copy row transforms reduce the row
