@@ -289,28 +289,34 @@ def run_ours(args):
         flush.fill_(1.0)
         plan.solve(sg, sd, out=out)
     torch.cuda.synchronize()
+    # the timed steps: plain solves, as a caller runs them (L2 flushed before each)
     clocks = ClockSampler(dev.index)
     clocks.start()
     time.sleep(0.1)
     barrier(world)
     torch.cuda.synchronize()
     t_begin = time.time()
-    lib, handle = plan._lib, plan._h
     for k in range(K):
         flush.fill_(1.0)
-        e = ev[k]
-        arr = (ctypes.c_void_p * 4)(*[x.cuda_event for x in e[1:5]])
-        if lib.sg_set_stage_events(handle, arr) != 0:
-            raise RuntimeError("sg_set_stage_events failed")
-        e[0].record()
+        ev[k][0].record()
         plan.solve(sg, sd, out=out)
-        e[5].record()
+        ev[k][5].record()
     torch.cuda.synchronize()
     barrier(world)
     t_end = time.time()
-    lib.sg_set_stage_events(handle, None)
     clk = clocks.stop(t_begin, t_end)
     step_ms = [e[0].elapsed_time(e[5]) for e in ev]
+    # the stage breakdown: a second pass with events between the launches (such
+    # solves keep plain stream order, so each stage's events bracket its kernel)
+    lib, handle = plan._lib, plan._h
+    for k in range(K):
+        flush.fill_(1.0)
+        arr = (ctypes.c_void_p * 4)(*[x.cuda_event for x in ev[k][1:5]])
+        if lib.sg_set_stage_events(handle, arr) != 0:
+            raise RuntimeError("sg_set_stage_events failed")
+        plan.solve(sg, sd, out=out)
+    torch.cuda.synchronize()
+    lib.sg_set_stage_events(handle, None)
     stage = {"rows_fwd": [], "cols": [], "rows_inv": []}
     ms3 = (ctypes.c_float * 3)()
     for e in ev:
@@ -338,6 +344,19 @@ def run_ours(args):
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": profiled_traffic() if args.engine == "fft32" else None,
                 "peak_source": f"{peak_kind} HBM copy bandwidth", "algorithmic_bytes_per_launch": col_bytes}
+    # the column pass against the FP32 arithmetic peak (it is issue-bound, so neither fraction saturates):
+    # nominal 5 L log2 L flops per length-L transform and 8 L per source-kernel product, against
+    # 152 SMs x 128 FP32 lanes x 2 flops x the median SM clock sampled during the timed steps
+    L = 2 * nr
+    fft_flops = 5 * L * int(np.log2(L))
+    col_flops = N * (nsrc * fft_flops + nsrc * ncomp * (fft_flops + 8 * nsrc * L))
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    compute = {"bound": "alu", "kernel": kname, "achieved": round(col_flops / (col_ms * 1e-3) / 1e12, 2),
+               "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+               "frac": round(col_flops / (col_ms * 1e-3) / 1e12 / fp32_peak, 4), "flops_per_launch": col_flops,
+               "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x median SM clock",
+               "model": "5 L log2 L per transform, 8 L per product"}
     # whole step against the 3-pass model traffic (60 B/cell gas-only with Phi)
     # col_bytes holds the spectra read, the kernel spectra and the column output written; add the inputs,
     # the row spectra written, the column output read back and the outputs written
@@ -367,6 +386,7 @@ def run_ours(args):
               "data": "synthetic (seeded log-normal disc, no dataset)",
               "config": dict(config_of(args, d), **({} if args.engine == "fft32" else {"column_engine": args.engine})),
               "roofline": roofline,
+              "compute": compute,
               "step_roofline": {"model_bytes_per_step": step_bytes, "frac": round(step_frac, 4),
                                 "compulsory_bytes_per_step": min_bytes,
                                 "compulsory_frac": round(min_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
