@@ -335,7 +335,7 @@ def run_ours(args):
     nsrc = 2 if d.sigma_d is not None else 1
     ncomp = len(outputs_of(args))
     N, nr = d.nphi // 2, d.nr
-    col_bytes = 8 * (nsrc * N * nr + nsrc * nsrc * ncomp * (N + 1) * nr + nsrc * ncomp * N * nr)
+    col_bytes, step_bytes, min_bytes = solve_model_bytes(nr, d.nphi, nsrc, ncomp)
     col_ms = statistics.mean(stage["cols"])
     peak, peak_kind = measured_peaks()
     achieved = col_bytes / (col_ms * 1e-3) / 1e9
@@ -358,12 +358,7 @@ def run_ours(args):
                "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flops x median SM clock",
                "model": "5 L log2 L per transform, 8 L per product"}
     # whole step against the 3-pass model traffic (60 B/cell gas-only with Phi)
-    # col_bytes holds the spectra read, the kernel spectra and the column output written; add the inputs,
-    # the row spectra written, the column output read back and the outputs written
-    step_bytes = col_bytes + 8 * nsrc * N * nr + 4 * nsrc * d.cells + 8 * nsrc * ncomp * N * nr + 4 * nsrc * ncomp * d.cells
     step_frac = step_bytes / (ms_per_step * 1e-3) / 1e9 / peak
-    # compulsory traffic: the sources, the kernel spectra and the outputs (28 B/cell gas-only with Phi)
-    min_bytes = 4 * nsrc * d.cells + 8 * nsrc * nsrc * ncomp * (N + 1) * nr + 4 * nsrc * ncomp * d.cells
 
     # ---- end to end through the C ABI with host buffers (pinned)
     hin_g = torch.from_numpy(d.sigma_g.astype(np.float32)).pin_memory()
@@ -445,6 +440,22 @@ def run_reference(args):
                          "sample": f"{K} FP64 FFT-convolution solves of the full disc (numpy, one core; "
                                    f"kernel spectra precomputed); steps capped at 8 to bound the run"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def solve_model_bytes(nr, nphi, nsrc, ncomp):
+    """Algorithmic HBM bytes of one FP32 FFT solve with `ncomp` components per
+    target fluid: (column pass, whole 3-pass step, compulsory).  The column
+    pass reads the row spectra and the kernel spectra (nsrc tables per
+    output, (nphi/2 + 1) x nr complex each) and writes the column output;
+    the step adds the sources, the row spectra written, the column output
+    read back and the outputs; the compulsory traffic is the sources, the
+    kernel spectra and the outputs.  Gas only with Phi: 28, 60 and 28 B/cell."""
+    N, cells = nphi // 2, nr * nphi
+    tables = 8 * nsrc * nsrc * ncomp * (N + 1) * nr
+    col = 8 * nsrc * N * nr + tables + 8 * nsrc * ncomp * N * nr
+    step = col + 8 * nsrc * N * nr + 4 * nsrc * cells + 8 * nsrc * ncomp * N * nr + 4 * nsrc * ncomp * cells
+    compulsory = 4 * nsrc * cells + tables + 4 * nsrc * ncomp * cells
+    return col, step, compulsory
 
 
 def step_model_bytes(nr, nphi, nsrc, nout, esz=4):

@@ -1,0 +1,53 @@
+"""The benchmark's traffic model and argument parsing, on the CPU: the byte
+counts behind every roofline fraction bench.py reports, derived here per cell
+from what each pass reads and writes."""
+import argparse
+
+import pytest
+
+import bench
+
+
+@pytest.mark.parametrize("nr,nphi", [(2048, 4096), (1024, 2048), (256, 512)])
+def test_gas_model_per_cell(nr, nphi):
+    """Gas only with Phi, g_r, g_phi (FP32): the column pass reads 4 B/cell of
+    row spectra and 3 x 4 B/cell of kernel spectra and writes 3 x 4 B/cell;
+    the step adds 4 (source) + 4 (row spectra written) + 12 (column output read
+    back) + 12 (outputs) B/cell; the compulsory traffic is source + kernel
+    spectra + outputs.  The kernel spectra hold one extra column (m = nphi/2)."""
+    cells, extra = nr * nphi, 3 * 8 * nr
+    col, step, comp = bench.solve_model_bytes(nr, nphi, 1, 3)
+    assert col == 28 * cells + extra
+    assert step == 60 * cells + extra
+    assert comp == 28 * cells + extra
+
+
+def test_bifluid_and_accel_only_per_cell():
+    nr, nphi = 512, 1024
+    cells = nr * nphi
+    # gas + dust with Phi: 8 sources, 16 row spectra, 48 kernel spectra, 48 column output, 24 outputs
+    _, step, comp = bench.solve_model_bytes(nr, nphi, 2, 3)
+    assert step == 144 * cells + 12 * 8 * nr
+    assert comp == 80 * cells + 12 * 8 * nr
+    # gas, accelerations only: 4 + 4 + 4 + 8 + 8 + 8 + 8 = 44 B/cell
+    _, step, _ = bench.solve_model_bytes(nr, nphi, 1, 2)
+    assert step == 44 * cells + 2 * 8 * nr
+
+
+@pytest.mark.parametrize("nr,nphi,nsrc", [(1024, 2048, 2), (128, 256, 2), (2048, 4096, 1)])
+def test_batch_model_agrees_with_solve_model(nr, nphi, nsrc):
+    """The batch line's per-disc model counts the kernel spectra at their
+    stored pitch (nr + 2 slots); otherwise it is the same sum."""
+    _, step, _ = bench.solve_model_bytes(nr, nphi, nsrc, 3)
+    b = bench.step_model_bytes(nr, nphi, nsrc, 3 * nsrc)
+    pad = 8 * nsrc * 3 * nsrc * (nphi // 2 + 1) * 2
+    assert b == step + pad
+
+
+def test_outputs_option():
+    ns = lambda v: argparse.Namespace(outputs=v)
+    assert bench.outputs_of(ns("phi,gr,gphi")) == ("phi", "gr", "gphi")
+    assert bench.outputs_of(ns("gr, gphi")) == ("gr", "gphi")
+    for bad in ("", "gr,gr", "phi,xx"):
+        with pytest.raises(SystemExit):
+            bench.outputs_of(ns(bad))
