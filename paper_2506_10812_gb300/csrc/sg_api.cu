@@ -313,15 +313,21 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     void *dev_out[6];
     for (int q = 0; q < 6; ++q) dev_out[q] = host_out[q] ? stg + (2 + q) * bytes : nullptr;
     const uint32_t mask = outmask_of(pl, dev_out);
+    // Inputs go up in nin chunks, each chunk's row transforms starting as it
+    // lands; outputs come down in two copies per output: inverse-row chunk 0
+    // alone (the copies start early) and chunks 1 .. nch-1 together, which
+    // finish on the GPU while the first copy is still running (each copy call
+    // costs ~2.5 us on the host link, so fewer and larger copies save time).
     const int rpc = row_rpc(nphi, pl->f64);
+    const int nin = nr / rpc < 4 ? nr / rpc : 4, rows_in = nr / nin;
     const int nch = nr / rpc < 8 ? nr / rpc : 8, rows = nr / nch;
     cudaStream_t c = pl->cstream;
     cudaEvent_t *ein = pl->cev, *eout = pl->cev + 8, start = pl->cev[16];
     unsigned int *flag = (pl->p.flags & SG_CHECK_FINITE) ? pl->flag : nullptr;
     cudaError_t e = cudaEventRecord(start, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c, start, 0);
-    for (int k = 0; k < nch && e == cudaSuccess; ++k) {
-        const size_t off = (size_t)k * rows * row_b, len = (size_t)rows * row_b;
+    for (int k = 0; k < nin && e == cudaSuccess; ++k) {
+        const size_t off = (size_t)k * rows_in * row_b, len = (size_t)rows_in * row_b;
         e = cudaMemcpyAsync((char *)dsg + off, (const char *)hsg + off, len, cudaMemcpyHostToDevice, c);
         if (e == cudaSuccess && dsd)
             e = cudaMemcpyAsync((char *)dsd + off, (const char *)hsd + off, len, cudaMemcpyHostToDevice, c);
@@ -329,7 +335,7 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ein[k], 0);
         if (e == cudaSuccess)
             e = launch_rows_fwd<R>(dsg, dsd, pl->nsrc, pl->sh, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen,
-                                   true, s, k * rows, rows, pl->tm_rows ? &pl->tm_sh : nullptr, pl->flag);
+                                   true, s, k * rows_in, rows_in, pl->tm_rows ? &pl->tm_sh : nullptr, pl->flag);
     }
     if (e != cudaSuccess) return cuda_fail(pl, e, "pipelined input and row transform");
     if (!mask) return cuda_fail(pl, cudaStreamSynchronize(s), "solve");
@@ -348,9 +354,12 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     for (int k = 0; k < nch && e == cudaSuccess; ++k) {
         e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, k * rows,
                                rows, pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag);
+        if (k != 0 && k != nch - 1) continue;
+        // copy group: chunk 0, then chunks 1 .. nch-1
+        const int k0 = k == 0 ? 0 : 1;
         if (e == cudaSuccess) e = cudaEventRecord(eout[k], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(c, eout[k], 0);
-        const size_t off = (size_t)k * rows * row_b, len = (size_t)rows * row_b;
+        const size_t off = (size_t)k0 * rows * row_b, len = (size_t)(k - k0 + 1) * rows * row_b;
         for (int q = 0; q < 6 && e == cudaSuccess; ++q)
             if ((mask >> q) & 1u)
                 e = cudaMemcpyAsync((char *)host_out[q] + off, (const char *)dev_out[q] + off, len,
