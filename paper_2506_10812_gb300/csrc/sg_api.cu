@@ -341,7 +341,8 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     if (!mask) return cuda_fail(pl, cudaStreamSynchronize(s), "solve");
     e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
                                      pl->flag, s)
-                   : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s);
+                   : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s, 0,
+                                    true);
     if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
     RowOut ro{};
     for (int q = 0; q < 6; ++q) {
@@ -352,8 +353,9 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
         ++ro.n;
     }
     for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+        // chunk 0 follows the column pass directly: a programmatic dependent of it
         e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, k * rows,
-                               rows, pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag);
+                               rows, pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag, k == 0);
         if (k != 0 && k != nch - 1) continue;
         // copy group: chunk 0, then chunks 1 .. nch-1
         const int k0 = k == 0 ? 0 : 1;
