@@ -262,6 +262,8 @@ def test_potential_accel_host_and_graph_agree_with_solve():
     (8, 64, True, torch.float32, ("phi", "gr", "gphi")),       # 2 row chunks
     (16, 32, False, torch.float64, ("gr",)),                    # 4 chunks, FP64, one output
     (512, 2048, True, torch.float32, ("gphi", "phi")),          # 8 chunks, compile-time rows
+    (64, 1024, True, torch.float32, ("phi", "gr", "gphi")),     # tensor-copy rows of 1024 at chunk offsets
+    (32, 512, False, torch.float32, ("gr",)),                   # tensor-copy rows of 512, 8 output chunks
     (2048, 4096, False, torch.float32, ("phi", "gr", "gphi"))])  # the benchmark disc
 def test_solve_host_pipeline_equals_solve(nr, nphi, bif, dtype, outs):
     """sg_solve_host copies and transforms in row chunks on two streams; the
