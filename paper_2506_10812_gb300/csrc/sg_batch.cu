@@ -1,6 +1,9 @@
 // Many independent discs in one persistent launch (the paper evolves one
 // disc per run and precomputes its kernel once, Sec. 5.2; here a batch of
 // FFT plans, uneven grids, gas-only or gas + dust, is solved together).
+// The batch's other engine (configure_streams, host side at the end) does not
+// use this kernel: it captures every disc's sg_solve launch chain on forked
+// streams of the batch's graph; the autotuner times both engines.
 //
 // Work decomposition.  A disc's FFT solve has three stages (the arithmetic is
 // that of sg_kernels.cu, see its header): row R2C of every source, the

@@ -9,15 +9,18 @@
 //             coefficients as re + i im) stored column-major;
 //   cols      per column m: zero-padded length-L forward FFT of every
 //             source, products with the kernel spectra (staged in shared
-//             memory by TMA bulk copies issued at kernel start) summed over
-//             sources (Sec. 5.2 multi-fluid sums), inverse FFT of every
-//             requested (target, component), rows 0..nr-1 written back;
+//             memory by TMA bulk copies, all at kernel start or one
+//             (target, component) step at a time) summed over sources (Sec.
+//             5.2 multi-fluid sums), inverse FFT of every requested (target,
+//             component), rows 0..nr-1 written back;
 //   rows_inv  per output row: packed C2R (length nphi) and the epilogue.
+// The column pass and the inverse rows launch as programmatic dependents of
+// the kernel before them (launch_ex; griddep_wait before reading its output).
 //
 // Layout of the [N][rows] intermediates (sg_mem.cuh, BW = 1): column-major,
 // element (m, i) at m rows + i, so the column pass moves contiguous columns
-// and a row transform that owns 4 consecutive rows moves a 32-byte slice of
-// every column.  (The column-blocked variant BW = 4, element (m, i) at
+// and a row transform that owns 2 or 4 consecutive rows moves a 16- or
+// 32-byte slice of every column.  (The column-blocked variant BW = 4, element (m, i) at
 // ((m / 4) rows + i) 4 + m % 4, gives the row transforms whole 128-byte
 // lines but makes every column access a stride-4 vector; on the 2048 x 4096
 // disc it makes the column pass 44 % slower and the row transforms 14 %
@@ -75,7 +78,7 @@ cudaError_t launch_ex(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem
 }
 
 // ----------------------------------------------------------------- sizes
-// Rows per CTA of the row transforms: up to SG_ROW_RPC (4; 8 measured
+// Rows per CTA of the transpose row kernels: up to SG_ROW_RPC (4; 8 measured
 // slower: 1024-thread CTAs with 139 KB of shared memory), at most 1024
 // threads (nphi / 32 per row) and 160 KB of shared memory.
 #ifndef SG_ROW_RPC
@@ -646,11 +649,13 @@ __device__ __noinline__ void col0_recompute(const cplx<R> *__restrict__ sh, cons
     }
 }
 
-// Columns m >= 1 of an FP32 gas + dust plan: both source spectra stay in
-// registers, and the kernel spectra of one (target, component) step (one per
-// source) are staged at a time; the next step's copy is issued once the
-// products have read the buffer, so it lands during the inverse transform.
-// 2 CTAs per SM instead of 1 (66 KB of shared memory at 2 nr = 4096).
+// Columns m >= 1 of a plan that stages kernel spectra per step (cols_steps):
+// the source spectra stay in registers, and the kernel spectra of one
+// (target, component) step (one table per source) are staged at a time; the
+// next step's copy is issued once the products have read the buffer, so it
+// lands during the inverse transform.  Gas + dust at 2 nr = 4096: 66 KB of
+// shared memory and 2 CTAs per SM instead of 197 KB and 1; gas only: 51 KB,
+// 80 registers and 3 CTAs per SM instead of 2.
 template <typename R, int LC, int NS>
 __device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
                                                 cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
