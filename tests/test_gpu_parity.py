@@ -390,22 +390,29 @@ def test_errors_and_finite_check():
         plan.sync()                       # flag cleared
 
 
-def test_column_pass_component_subsets_1024x2048():
+@pytest.mark.parametrize("nr,nphi,bif", [
+    (1024, 2048, False),    # columns of 2048: all requested spectra staged at once
+    (2048, 4096, False),    # columns of 4096: one component staged per step (gas only)
+    (1024, 4096, True)])    # gas + dust, columns of 2048: one (target, component) step at a time
+def test_column_pass_component_subsets(nr, nphi, bif):
     """The FP32 column pass at the compile-time lengths stages one, two or
-    three kernel spectra (potential only, accelerations only, all): each
-    subset equals the fused solve exactly."""
-    d = inputs.lognormal_gas(1024, 2048, offset=7)
+    three kernel spectra per target (potential only, accelerations only, one
+    component, all, and for gas + dust one target's outputs only): each subset
+    equals the fused solve exactly."""
+    d = inputs.lognormal_bifluid(nr, nphi, St=0.1, offset=7) if bif else inputs.lognormal_gas(nr, nphi, offset=7)
     dev = torch.device("cuda:0")
-    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, None, G=d.G) as plan:
+    with P()(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G) as plan:
         sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
-        full = plan.solve(sg)
-        pot = plan.potential(sg)
-        acc = plan.accel(sg)
-        only_r = plan.solve(sg, outputs=("gr",))
+        sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=torch.float32, device=dev)
+        full = plan.solve(sg, sd)
+        subsets = [plan.potential(sg, sd), plan.accel(sg, sd), plan.solve(sg, sd, outputs=("gr",)),
+                   plan.solve(sg, sd, outputs=("gphi", "phi"))]
+        if bif:
+            subsets.append(plan.solve(sg, sd, out={"gphi_d": torch.empty_like(full["gphi_d"])}))
         torch.cuda.synchronize()
-    assert torch.equal(pot["phi_g"], full["phi_g"])
-    assert torch.equal(acc["gr_g"], full["gr_g"]) and torch.equal(acc["gphi_g"], full["gphi_g"])
-    assert torch.equal(only_r["gr_g"], full["gr_g"])
+    for sub in subsets:
+        for k, v in sub.items():
+            assert torch.equal(v, full[k]), k
 
 
 # ---------------------------------------------------------- indirect term
