@@ -184,7 +184,7 @@ def test_lognormal_full_size(nr, nphi):
         assert np.abs(ref[k].ravel()[idx] - samp[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
 
 
-@pytest.mark.parametrize("nr,nphi,St", [(512, 1024, 1.0), (1024, 2048, 0.1)])
+@pytest.mark.parametrize("nr,nphi,St", [(512, 1024, 1.0), (1024, 2048, 0.1), (2048, 4096, 0.1)])
 def test_lognormal_bifluid_large(nr, nphi, St):
     d = rounded(inputs.lognormal_bifluid(nr, nphi, St=St), torch.float32)
     ref = oracle.fft64(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G)
