@@ -239,7 +239,7 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
         e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
                                          sflag, s)
                        : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, sflag, s,
-                                        0, !ev);
+                                        0, !ev, true);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
         RowOut ro{};
@@ -342,7 +342,7 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
                                      pl->flag, s)
                    : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s, 0,
-                                    true);
+                                    true, true);
     if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
     RowOut ro{};
     for (int q = 0; q < 6; ++q) {

@@ -66,11 +66,13 @@ int rows_tma_inv_rows();
 // flag: bit 2 set when a staged copy never completed (bounded wait).
 // ncols > 0: only columns 0 .. ncols - 1.  pdl: programmatic dependent
 // launch on the row transform before it (the set-up and the first kernel-
-// spectrum copies overlap that kernel's last CTAs).
+// spectrum copies overlap that kernel's last CTAs).  discard: the row spectra
+// are dead once read, so each column's L2 lines are discarded after its
+// forward transform (never written back; the caller reads sh no more).
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
                         uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols = 0,
-                        bool pdl = false);
+                        bool pdl = false, bool discard = false);
 
 // Column pass with tensor-core DFT stages (sg_dftmma.cu): FP32 gas-only
 // plans with 2 nr in {2048, 4096}; engine 1..4 as SG_ENGINE_DFT_*; atab

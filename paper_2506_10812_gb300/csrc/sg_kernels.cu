@@ -252,13 +252,13 @@ constexpr int rows_tma_min_blocks(int NC, int NR, int sm_threads)
 {
     return sm_threads / rows_tma_threads(NC, NR) < 32 ? sm_threads / rows_tma_threads(NC, NR) : 32;
 }
+int rows_tma_fwd_rows() { return kRowsFwdNR; }
+int rows_tma_inv_rows() { return kRowsInvNR; }
 size_t row_tma_smem_bytes(int N, int NR)
 {
     const size_t tile = (size_t)N * NR * 8, xb = (size_t)NR * row_pitch_tma(N, NR) * 8;
     return kRowHdr + (tile > xb ? tile : xb);
 }
-int rows_tma_fwd_rows() { return kRowsFwdNR; }
-int rows_tma_inv_rows() { return kRowsInvNR; }
 
 // cos(2 pi e / 32), e = 0..8
 __device__ constexpr double kCos32[9] = {1.0,
@@ -660,7 +660,7 @@ template <typename R, int LC, int NS>
 __device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
                                                 cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
                                                 const cplx<R> *__restrict__ tw, unsigned int *flag, cplx<R> *xb,
-                                                cplx<R> *tb, uint64_t *bar, int m)
+                                                cplx<R> *tb, uint64_t *bar, int m, int discard)
 {
     using C = cplx<R>;
     const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
@@ -696,6 +696,9 @@ __device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, 
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
         fft_any<true, LC>(v, L, T, t, xb, tw);
+        // every thread's loads of this column were consumed before the
+        // transform's first barrier: the column is dead
+        if (discard) l2_discard_range(sh + (size_t)a * N * nr + blk(m, 0, nr), (size_t)nr * sizeof(C), t, T);
 #pragma unroll
         for (int e = 0; e < 16; ++e) spec[a][e] = v[e];
     }
@@ -734,7 +737,7 @@ __device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, 
 template <typename R, int NS, int LC>
 __global__ void __launch_bounds__(cols_max_threads(NS, sizeof(R) == 8, LC), cols_min_blocks(NS, sizeof(R) == 8, LC))
 k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr_rt,
-       int N, uint32_t outmask, const cplx<R> *__restrict__ tw, unsigned int *flag)
+       int N, uint32_t outmask, const cplx<R> *__restrict__ tw, unsigned int *flag, int discard)
 {
     using C = cplx<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -755,7 +758,7 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
         return;
     }
     if constexpr (PAIR) {
-        cols_pair_steps<R, LC, NS>(sh, tab, oh, nr, N, outmask, tw, flag, xb, tb, bar, m);
+        cols_pair_steps<R, LC, NS>(sh, tab, oh, nr, N, outmask, tw, flag, xb, tb, bar, m, discard);
         return;
     }
     C *sspec = tb + (size_t)NS * 3 * P;           // NS == 2: source spectra in shared memory
@@ -792,6 +795,9 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
         fft_any<true, LC>(v, L, T, t, xb, tw);
+        // every thread's loads of this column were consumed before the
+        // transform's first barrier: the column is dead
+        if (discard) l2_discard_range(sh + (size_t)a * N * nr + blk(m, 0, nr), (size_t)nr * sizeof(C), t, T);
         if constexpr (NS == 1) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) spec[e] = v[e];
@@ -842,16 +848,20 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
 
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
-                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols, bool pdl)
+                        uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols, bool pdl,
+                        bool discard)
 {
     const bool f64 = sizeof(R) == 8;
     const int N = nphi / 2, T = (2 * nr) / 16;
     const size_t smem = col_smem_bytes(nr, nsrc, f64);
     const int grid = ncols > 0 && ncols < N ? ncols : N;
+    // whole 128-byte lines per source column (column 0 is read more than once
+    // by its CTA and never discarded)
+    const bool dc = discard && BW == 1 && ((size_t)nr * 2 * sizeof(R)) % 128 == 0 && ((uintptr_t)sh & 127u) == 0;
     cudaError_t err = cudaSuccess;
     auto go = [&](auto kern) {
         err = launch_ex(kern, dim3(grid), dim3(T), smem, s, pdl, (const cplx<R> *)sh, (const cplx<R> *)tab,
-                        (cplx<R> *)oh, nr, N, outmask, (const cplx<R> *)tw_col, flag);
+                        (cplx<R> *)oh, nr, N, outmask, (const cplx<R> *)tw_col, flag, dc ? 1 : 0);
     };
     const int L = 2 * nr;
     if (nsrc == 1) {
@@ -1130,8 +1140,8 @@ cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, c
         if (tm && rows_tma_eligible(nr, nphi, false)) {
             const dim3 gt(nrows_run / kRowsInvNR, o.n);
             auto go = [&](auto kern, int N) {
-                err = launch_ex(kern, gt, dim3(kRowsInvNR * N / 16), row_tma_smem_bytes(N, kRowsInvNR), s, pdl, *tm, o,
-                                (const float2 *)tw_row, (const float2 *)twp_row, rcen, flag, tflag, row0);
+                err = launch_ex(kern, gt, dim3(kRowsInvNR * N / 16), row_tma_smem_bytes(N, kRowsInvNR), s, pdl, *tm,
+                                o, (const float2 *)tw_row, (const float2 *)twp_row, rcen, flag, tflag, row0);
             };
             if (nphi == 4096) go(k_rows_inv_tma<2048>, 2048);
             else if (nphi == 2048) go(k_rows_inv_tma<1024>, 1024);
@@ -1186,9 +1196,9 @@ template cudaError_t launch_rows_fwd<double>(const double *, const double *, int
                                              const void *, const double *, bool, cudaStream_t, int, int,
                                              const CUtensorMap *, unsigned int *);
 template cudaError_t launch_cols<float>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
-                                        unsigned int *, cudaStream_t, int, bool);
+                                        unsigned int *, cudaStream_t, int, bool, bool);
 template cudaError_t launch_cols<double>(const void *, const void *, void *, int, int, int, uint32_t, const void *,
-                                         unsigned int *, cudaStream_t, int, bool);
+                                         unsigned int *, cudaStream_t, int, bool, bool);
 template cudaError_t launch_tabcols<float>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_tabcols<double>(const void *, void *, int, int, bool, const void *, cudaStream_t);
 template cudaError_t launch_rows_inv<float>(const void *, const RowOut &, int, int, const void *, const void *,

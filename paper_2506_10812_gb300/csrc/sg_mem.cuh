@@ -183,4 +183,72 @@ __device__ __forceinline__ void mbar_inval(uint64_t *bar)
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// ---------------------------------------------- dead-data L2 discards
+// The spectral intermediates are written into L2 by one kernel and read once
+// by the next.  Once read they are dead, but L2 is write-back: left alone,
+// every such line is written to DRAM when it is evicted (and, under pressure,
+// lines not yet read are evicted and fetched again).  discard.global.L2
+// invalidates a 128-byte line without writing it back; it is issued only for
+// lines every reader has finished with, and nothing reads them again before
+// the next solve rewrites them.
+__device__ __forceinline__ void l2_discard(const void *p)
+{
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+// Discard the `bytes` (a multiple of 128, 128-byte aligned) at p, the lines
+// spread over the `nthr` threads of the caller (thread index `tid`).
+__device__ __forceinline__ void l2_discard_range(const void *p, size_t bytes, int tid, int nthr)
+{
+    const char *c = reinterpret_cast<const char *>(p);
+    for (size_t off = (size_t)tid * 128; off < bytes; off += (size_t)nthr * 128) l2_discard(c + off);
+}
+
+
+// ------------------------------------------------- tensor memory (TMEM)
+// Each SM's tensor memory is 128 lanes x 512 columns of 32-bit cells.  With
+// the 32x32b shapes a warp reaches the 32 lanes 32 (warp % 4) .. + 31 only:
+// thread l of the warp is lane 32 (warp % 4) + l, and register j of a
+// transfer is column col + j.  An address is (lane << 16) | column.
+// Allocation (a power of two >= 32 columns) and release are whole-warp
+// operations of one warp; a CTA must release what it allocated before it exits.
+__device__ __forceinline__ void tmem_alloc(uint32_t *smem_dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(smem_dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// around a CTA barrier that orders tensor-memory accesses
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 8 complex FP32 values (16 cells) of this thread's lane, from column col of
+// taddr on; each call waits for its own transfer, so the registers are
+// written (load) or free (store) when it returns.
+__device__ __forceinline__ void tmem_st8c(uint32_t taddr, const float2 (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16};\n\ttcgen05.wait::st.sync.aligned;" ::"r"(taddr),
+                 "f"(v[0].x), "f"(v[0].y), "f"(v[1].x), "f"(v[1].y), "f"(v[2].x), "f"(v[2].y), "f"(v[3].x),
+                 "f"(v[3].y), "f"(v[4].x), "f"(v[4].y), "f"(v[5].x), "f"(v[5].y), "f"(v[6].x), "f"(v[6].y),
+                 "f"(v[7].x), "f"(v[7].y)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld8c(uint32_t taddr, float2 (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x), "=f"(v[2].y), "=f"(v[3].x),
+                   "=f"(v[3].y), "=f"(v[4].x), "=f"(v[4].y), "=f"(v[5].x), "=f"(v[5].y), "=f"(v[6].x),
+                   "=f"(v[6].y), "=f"(v[7].x), "=f"(v[7].y)
+                 : "r"(taddr)
+                 : "memory");
+}
+
 }  // namespace sg
