@@ -202,11 +202,18 @@ sg_status sg_stage_times(void *const *events, float *ms);
  * library (every GPU that loads the library keeps it until the process
  * exits), so grids are limited to nr <= 1024 and nphi <= 4096; larger grids
  * return SG_ERR_UNSUPPORTED with a message on stderr.  The call allocates
- * and frees nothing.  Its first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) for that device, so make that first
- * call before any stream capture.  Every call shares the array and rewrites
+ * and frees nothing.  Its first call in a CUDA context looks up the array's
+ * device address (cudaGetSymbolAddress) for that context, so make that first
+ * call before any stream capture; after cudaDeviceReset the next call looks
+ * it up again in the new context.  Every call shares the array and rewrites
  * the part it reads before reading it; calls whose GPU work overlaps (two
- * streams, two host threads) race on it, so serialise them.               */
+ * streams, two host threads) race on it, so serialise them.
+ *
+ * Errors: SG_ERR_ARG for the parameter sets sg_plan_create rejects (h_g,
+ * h_d not finite, h_g <= 0 without H_g_field, a second fluid without
+ * sigma_d ...); SG_ERR_CUDA, with nothing launched, when a CUDA error is
+ * already pending on the calling thread (left unconsumed for the caller to
+ * read), or when a launch of this call fails.                              */
 sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, const void *sigma_d,
                             void *phi_g, void *gr_g, void *gphi_g,
                             void *phi_d, void *gr_d, void *gphi_d, void *stream);

@@ -221,11 +221,46 @@ __global__ void k_direct_geometry(int nr, int nphi, double r_in, double du, R *g
 
 namespace {
 
+// The array's device address, looked up once per CUDA context.  A context is
+// identified by its unique id (cuCtxGetId: never reused within a process), so
+// a primary context that cudaDeviceReset tore down and the runtime created
+// again gets a fresh lookup instead of the old, dangling address.
+struct NoAllocSlot {
+    unsigned long long ctx_id;
+    void *ptr;
+};
 std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[64] = {nullptr};
+NoAllocSlot g_noalloc[64] = {};
 
-// Device address of the array for the current device, looked up once per
-// device (the first call on a device does the lookup).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context; 0 when none is current.
+unsigned long long current_ctx_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the array in the current context: the lookup runs on the
+// first call in each context (it also makes the device's primary context
+// current when none is), later calls reuse it.
 cudaError_t noalloc_scratch(void **out)
 {
     int dev = -1;
@@ -233,13 +268,16 @@ cudaError_t noalloc_scratch(void **out)
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocSlot &slot = g_noalloc[dev];
+    const unsigned long long id = current_ctx_id();
+    if (id == 0 || id != slot.ctx_id || !slot.ptr) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_sg_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = ptr;
+        slot.ptr = ptr;
+        slot.ctx_id = current_ctx_id();            // nonzero once the lookup made a context current
     }
-    *out = g_noalloc_ptr[dev];
+    *out = slot.ptr;
     return cudaSuccess;
 }
 
@@ -284,9 +322,18 @@ extern "C" sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, 
                 p->nphi, kNoAllocMaxNr, kNoAllocMaxNphi);
         return SG_ERR_UNSUPPORTED;
     }
-    if (!(p->h_g > 0 || p->H_g_field)) return SG_ERR_ARG;
+    // the parameter sets sg_plan_create accepts for a DIRECT plan
+    if (!(std::isfinite(p->h_g) && (p->h_g > 0 || p->H_g_field))) return SG_ERR_ARG;
     const int nsrc = (p->h_d > 0 || p->H_d_field) ? 2 : 1;
-    if (nsrc == 2 && !sigma_d) return SG_ERR_ARG;
+    if (nsrc == 2 && (!std::isfinite(p->h_d) || !sigma_d)) return SG_ERR_ARG;
+    // an error left pending by the caller's own work is theirs: report it
+    // without consuming it, and launch nothing
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        fprintf(stderr, "sg_direct_noalloc: a CUDA error is already pending (%s); nothing launched\n",
+                cudaGetErrorString(pending));
+        return SG_ERR_CUDA;
+    }
     void *scratch = nullptr;
     cudaError_t e = noalloc_scratch(&scratch);
     if (e != cudaSuccess) {
