@@ -120,6 +120,50 @@ def test_direct_general_scale_heights(dtype, tol):
     assert_close(gpu_solve(d, dtype, method="direct", H_g=Hg, H_d=Hd), ref, tol, "directH")
 
 
+# ------------------------------------------- direct path at the C2 size
+def sample_targets(nr, nphi, n=512, seed=41):
+    """Seeded cell indices: n random cells plus the grid's corners, edges and
+    middle (inner and outer rings, phi = 0 and the last phi cell)."""
+    rng = np.random.default_rng(seed)
+    idx = set(rng.choice(nr * nphi, n, replace=False).tolist())
+    for i in (0, 1, nr // 2, nr - 2, nr - 1):
+        for j in (0, 1, nphi // 2, nphi - 1):
+            idx.add(i * nphi + j)
+    return np.array(sorted(idx), dtype=np.int64)
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, TOL32), (torch.float64, TOL64)])
+def test_direct_c2_size_st1_sampled(dtype, tol):
+    """Direct path (general-H pair sum) at 256 x 512, gas + dust with St = 1:
+    h_d = 1.58e-3, so X = d^2 / 8 reaches ~2e5 and the FP32 Bessel evaluator
+    runs its large-X branch for almost every dust pair.  Compared element by
+    element with the oracle's direct sum at 512 seeded cells plus the grid's
+    edges and corners, all six outputs."""
+    d = rounded(inputs.spiral_bifluid(St=1.0, nr=256, nphi=512), dtype)
+    idx = sample_targets(d.nr, d.nphi)
+    ref = oracle.direct(grid(d), d.sigma_g, d.sigma_d, h_g=d.h_g, h_d=d.h_d, G=d.G, targets=idx)
+    out = gpu_solve(d, dtype, method="direct")
+    assert set(out) == set(ref)
+    assert_close({k: v.ravel()[idx] for k, v in out.items()}, ref, tol, f"direct 256x512 {dtype}")
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float32, TOL32), (torch.float64, TOL64)])
+def test_direct_scale_height_fields_64x128(dtype, tol):
+    """Position-dependent scale heights at 64 x 128 (gas + dust, St = 1): each
+    cell's H is h r times a seeded factor in [0.6, 1.4]; the whole field
+    against the oracle."""
+    d = rounded(inputs.spiral_bifluid(St=1.0, nr=64, nphi=128), dtype)
+    R, _ = grid(d).mesh()
+    rng = np.random.default_rng(23)
+    Hg = R * d.h_g * rng.uniform(0.6, 1.4, R.shape)
+    Hd = R * d.h_d * rng.uniform(0.6, 1.4, R.shape)
+    if dtype == torch.float32:
+        Hg = Hg.astype(np.float32).astype(np.float64)
+        Hd = Hd.astype(np.float32).astype(np.float64)
+    ref = oracle.direct(grid(d), d.sigma_g, d.sigma_d, H_g=Hg, H_d=Hd, G=d.G)
+    assert_close(gpu_solve(d, dtype, method="direct", H_g=Hg, H_d=Hd), ref, tol, f"directH 64x128 {dtype}")
+
+
 def test_fft_fp32_small_gas():
     d = rounded(inputs.small_gas(), torch.float32)
     ref = oracle.direct(grid(d), d.sigma_g, h_g=d.h_g, G=d.G)
