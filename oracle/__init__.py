@@ -285,10 +285,24 @@ def fft64_plan(grid, h_g=0.05, h_d=None, G=1.0):
     return {"grid": grid, "fluids": [f for f, _ in fl], "G": G, "spectra": spectra}
 
 
-def fft64_apply(plan, sigma_g, sigma_d=None):
+def fft64_apply(plan, sigma_g, sigma_d=None, workers=None):
     """FP64 zero-padded FFT convolution (Sec. 5.2: log grid, radial padding to
     2 nr; App. C kernels; bi-fluid sums over sources as in Sec. 5.2's
-    multi-fluid equations, with one table per ordered pair)."""
+    multi-fluid equations, with one table per ordered pair).
+
+    ``workers``: None runs numpy's FFTs on one thread (the parity reference);
+    an integer runs the same FP64 transforms through scipy.fft on that many
+    threads (for timing the oracle on all of a host's cores)."""
+    if workers is None:
+        rfft2, irfft2 = np.fft.rfft2, np.fft.irfft2
+    else:
+        import scipy.fft as sf
+
+        def rfft2(a):
+            return sf.rfft2(a, workers=workers)
+
+        def irfft2(a, s):
+            return sf.irfft2(a, s=s, workers=workers)
     grid = plan["grid"]
     nr, nphi = grid.nr, grid.nphi
     srcs = {"g": _c64(sigma_g)}
@@ -298,7 +312,7 @@ def fft64_apply(plan, sigma_g, sigma_d=None):
     for name, sig in srcs.items():
         pad = np.zeros((2 * nr, nphi))
         pad[:nr] = sig
-        spec[name] = np.fft.rfft2(pad)
+        spec[name] = rfft2(pad)
     out = {}
     r = grid.r[:, None]
     scale = -plan["G"] * grid.du * grid.dphi
@@ -308,7 +322,7 @@ def fft64_apply(plan, sigma_g, sigma_d=None):
             tabs = plan["spectra"][(sname, tname)]
             for c in range(3):
                 acc[c] = acc[c] + spec[sname] * tabs[c]
-        res = [np.fft.irfft2(a, s=(2 * nr, nphi))[:nr] * scale for a in acc]
+        res = [irfft2(a, s=(2 * nr, nphi))[:nr] * scale for a in acc]
         out["phi_" + tname] = res[0] * r
         out["gr_" + tname] = res[1]
         out["gphi_" + tname] = res[2]
