@@ -20,8 +20,10 @@ SG_COMP_PHI, SG_COMP_R, SG_COMP_AZ = 0, 1, 2
 SG_CHECK_FINITE = 2
 SG_BATCH_HOST_GATE = 4
 SG_BATCH_ORDER_PIPELINED, SG_BATCH_ORDER_STAGED = 0, 1
-SG_ENGINE_FFT32, SG_ENGINE_DFT_FP16X3, SG_ENGINE_DFT_BF16X3, SG_ENGINE_DFT_FP16, SG_ENGINE_DFT_BF16 = range(5)
-ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf16": 4}
+SG_ENGINE_FFT32, SG_ENGINE_DFT_FP16X3, SG_ENGINE_DFT_BF16X3, SG_ENGINE_DFT_FP16, SG_ENGINE_DFT_BF16, \
+    SG_ENGINE_TC_BF16X3, SG_ENGINE_TC_TF32X3, SG_ENGINE_TC_BF16 = range(8)
+ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf16": 4,
+           "tc_bf16x3": 5, "tc_tf32x3": 6, "tc_bf16": 7}
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",

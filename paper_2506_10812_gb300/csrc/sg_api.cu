@@ -236,9 +236,11 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
                                sflag);
         if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
         if (ev) cudaEventRecord(pl->ev[1], s);
-        e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
-                                         sflag, s)
-                       : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, sflag, s,
+        e = pl->engine >= SG_ENGINE_TC_BF16X3
+                ? launch_cols_tc(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, sflag, s)
+            : pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
+                                           sflag, s)
+                         : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, sflag, s,
                                         0, !ev, true);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
@@ -339,9 +341,11 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     }
     if (e != cudaSuccess) return cuda_fail(pl, e, "pipelined input and row transform");
     if (!mask) return cuda_fail(pl, cudaStreamSynchronize(s), "solve");
-    e = pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
-                                     pl->flag, s)
-                   : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s, 0,
+    e = pl->engine >= SG_ENGINE_TC_BF16X3
+            ? launch_cols_tc(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->flag, s)
+        : pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
+                                       pl->flag, s)
+                     : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s, 0,
                                     true, true);
     if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
     RowOut ro{};
@@ -670,7 +674,7 @@ int32_t sg_launches_per_solve(const sg_plan *pl, uint32_t outmask)
 sg_status sg_set_column_engine(sg_plan *pl, int32_t engine)
 {
     if (!pl) return SG_ERR_ARG;
-    if (engine < SG_ENGINE_FFT32 || engine > SG_ENGINE_DFT_BF16) return fail(pl, SG_ERR_ARG, "unknown engine %d", engine);
+    if (engine < SG_ENGINE_FFT32 || engine > SG_ENGINE_TC_BF16) return fail(pl, SG_ERR_ARG, "unknown engine %d", engine);
     if (engine == SG_ENGINE_FFT32) {
         pl->engine = 0;
         return SG_OK;
@@ -680,6 +684,10 @@ sg_status sg_set_column_engine(sg_plan *pl, int32_t engine)
                     "tensor-core column engines need an FP32 gas-only FFT plan with nr = 1024 or 2048");
     sg_status st = check_device(pl);
     if (st != SG_OK) return st;
+    if (engine >= SG_ENGINE_TC_BF16X3) {
+        pl->engine = engine;
+        return SG_OK;
+    }
     uint32_t h[8 * 32 * 4];
     dftmma_frag_table(engine == SG_ENGINE_DFT_FP16X3 || engine == SG_ENGINE_DFT_FP16, h);
     cudaError_t e = cudaSuccess;

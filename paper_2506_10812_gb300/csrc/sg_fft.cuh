@@ -345,8 +345,16 @@ __device__ __forceinline__ void load_pass_tw(const T *__restrict__ tp, int t, T 
     }
 }
 
-template <bool FWD, int L, int Ns, typename T>
-__device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *__restrict__ tp, const T (&b)[12])
+// The radix-16 butterflies of the compile-time passes, in registers; a
+// policy with the same call operator (the tensor-core DFT engine) can stand
+// in for it.
+template <bool FWD> struct RegDft16 {
+    template <typename T> __device__ __forceinline__ void operator()(T (&v)[16]) const { dft16<FWD>(v); }
+};
+
+template <bool FWD, int L, int Ns, typename T, typename D16 = RegDft16<FWD>>
+__device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *__restrict__ tp, const T (&b)[12],
+                                            D16 &&d16 = D16{})
 {
     constexpr int TT = L / 16;
     if constexpr (Ns * 16 <= L) {
@@ -370,12 +378,12 @@ __device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *_
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[r] = twmul<FWD>(v[r], w[r]);
         }
-        dft16<FWD>(v);
+        d16(v);
         if constexpr (Ns * 16 < L) {
             T nb[12];
             load_pass_tw<L, Ns * 16>(tp + 15 * Ns, t, nb);
             exchange_ct<Ns, TT>(v, t, xb);
-            fft_ct_pass<FWD, L, Ns * 16>(v, t, xb, tp + 15 * Ns, nb);
+            fft_ct_pass<FWD, L, Ns * 16>(v, t, xb, tp + 15 * Ns, nb, d16);
         }
     } else {
         constexpr int RL = L / Ns, Q = 16 / RL;
@@ -408,24 +416,32 @@ __device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *_
     }
 }
 
-template <bool FWD, int L, typename T>
-__device__ __forceinline__ void fft_ct(T (&v)[16], int t, T *xb, const T *__restrict__ twp)
+template <bool FWD, int L, typename T, typename D16 = RegDft16<FWD>>
+__device__ __forceinline__ void fft_ct(T (&v)[16], int t, T *xb, const T *__restrict__ twp, D16 &&d16 = D16{})
 {
     static_assert(L >= 256 && (L & (L - 1)) == 0, "compile-time FFT needs a power of two >= 256");
-    dft16<FWD>(v);
+    d16(v);
     T b[12];
     load_pass_tw<L, 16>(twp, t, b);
     exchange_ct<1, L / 16>(v, t, xb);
-    fft_ct_pass<FWD, L, 16>(v, t, xb, twp, b);
+    fft_ct_pass<FWD, L, 16>(v, t, xb, twp, b, d16);
 }
 
-// Compile-time length when LC > 0, runtime length L otherwise.
-template <bool FWD, int LC, typename T>
-__device__ __forceinline__ void fft_any(T (&v)[16], int L, int T_, int t, T *xb, const T *__restrict__ twp)
+// Compile-time length when LC > 0, runtime length L otherwise (the
+// butterfly policy d16 applies to the compile-time lengths).
+template <bool FWD, int LC, typename T, typename D16 = RegDft16<FWD>>
+__device__ __forceinline__ void fft_any(T (&v)[16], int L, int T_, int t, T *xb, const T *__restrict__ twp,
+                                        D16 &&d16 = D16{})
 {
-    if constexpr (LC > 0) fft_ct<FWD, LC>(v, t, xb, twp);
+    if constexpr (LC > 0) fft_ct<FWD, LC>(v, t, xb, twp, d16);
     else fft_reg<FWD>(v, L, T_, t, xb, twp);
 }
+
+// The butterfly policies of a column pass: the forward and the inverse
+// transforms' radix-16 DFTs (registers by default).
+struct RegEngine {
+    template <bool FWD> __device__ __forceinline__ RegDft16<FWD> d16() const { return {}; }
+};
 
 // Number of complex entries of the per-pass twiddle table of length L.
 __host__ __device__ constexpr int pass_twiddle_count(int L)

@@ -80,6 +80,11 @@ cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int n
 cudaError_t launch_cols_mma(int engine, const void *sh, const void *tab, void *oh, int nr, int nphi, uint32_t outmask,
                             const void *tw_col, const uint32_t *atab, unsigned int *flag, cudaStream_t s);
 size_t cols_mma_smem(int nr);
+
+// Column pass with tcgen05 DFT stages (sg_tcdft.cu): FP32 gas-only plans with
+// 2 nr in {2048, 4096}; engine SG_ENGINE_TC_*.
+cudaError_t launch_cols_tc(int engine, const void *sh, const void *tab, void *oh, int nr, int nphi, uint32_t outmask,
+                           const void *tw_col, unsigned int *flag, cudaStream_t s);
 // Host: the 8 x 32 x 4 A-fragment words (FP16 if f16, else BF16).
 void dftmma_frag_table(bool f16, uint32_t *out);
 

@@ -48,6 +48,7 @@
 #include <utility>
 
 #include "sg_bessel.cuh"
+#include "sg_cols.cuh"
 #include "sg_fft.cuh"
 #include "sg_internal.h"
 #include "sg_mem.cuh"
@@ -534,14 +535,6 @@ cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nr
 
 
 // ---------------------------------------------------------- column pass
-// Kernel spectrum of one (pair, component, column m): P = H + 2 complex,
-// slot k = S(k) for 0 <= k <= H (S(0), S(H) real); S(k > H) = conj(S(L - k)).
-template <typename C>
-__device__ __forceinline__ C spec_at(const C *col, int k, int H, bool upper)
-{
-    return upper ? cconj(col[2 * H - k]) : col[k];
-}
-
 // Column m = 0 holds the packed (m = 0, m = nphi/2) pair of real columns:
 // Z = A + i B, so P = A S0 + i B SN = ((Z + Z*(-k)) S0 + (Z - Z*(-k)) SN) / 2.
 template <typename R, int NS>
@@ -649,91 +642,6 @@ __device__ __noinline__ void col0_recompute(const cplx<R> *__restrict__ sh, cons
     }
 }
 
-// Columns m >= 1 of a plan that stages kernel spectra per step (cols_steps):
-// the source spectra stay in registers, and the kernel spectra of one
-// (target, component) step (one table per source) are staged at a time; the
-// next step's copy is issued once the products have read the buffer, so it
-// lands during the inverse transform.  Gas + dust at 2 nr = 4096: 66 KB of
-// shared memory and 2 CTAs per SM instead of 197 KB and 1; gas only: 51 KB,
-// 80 registers and 3 CTAs per SM instead of 2.
-template <typename R, int LC, int NS>
-__device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
-                                                cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
-                                                const cplx<R> *__restrict__ tw, unsigned int *flag, cplx<R> *xb,
-                                                cplx<R> *tb, uint64_t *bar, int m, int discard)
-{
-    using C = cplx<R>;
-    const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
-    const int t = threadIdx.x;
-    auto next_q = [&](int q) {
-        for (++q; q < 3 * NS; ++q)
-            if ((outmask >> q) & 1u) return q;
-        return -1;
-    };
-    auto issue = [&](int q) {
-        if (t == 0) {
-            const int b = q / 3, c = q % 3;
-            const uint64_t pol = l2_evict_first();
-            mbar_expect_tx(bar, (unsigned)(NS * P * sizeof(C)));
-#pragma unroll
-            for (int a = 0; a < NS; ++a)
-                tma_load_1d(tb + (size_t)a * P, tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1) + m) * P,
-                            P * sizeof(C), bar, pol);
-        }
-    };
-    int q = next_q(-1);
-    if (t == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (q >= 0) issue(q);                          // lands while the forward FFTs run
-    griddep_wait();                                // the row spectra are complete from here on
-    C spec[NS][16];
-#pragma unroll
-    for (int a = 0; a < NS; ++a) {
-        C v[16];
-        const uint64_t pf = l2_evict_first();
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(sh + (size_t)a * N * nr + blk(m, t + T * e, nr), pf);
-#pragma unroll
-        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
-        fft_any<true, LC>(v, L, T, t, xb, tw);
-        // every thread's loads of this column were consumed before the
-        // transform's first barrier: the column is dead
-        if (discard) l2_discard_range(sh + (size_t)a * N * nr + blk(m, 0, nr), (size_t)nr * sizeof(C), t, T);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) spec[a][e] = v[e];
-    }
-    for (int s = 0; q >= 0; ++s) {
-        const int b = q / 3, c = q % 3;
-        if (__syncthreads_or(!mbar_wait_bounded(bar, (unsigned)(s & 1), flag))) return;
-        C v[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int k = t + T * e;
-            C acc = mkc<C>(0, 0);
-#pragma unroll
-            for (int a = 0; a < NS; ++a) {
-                C S = spec_at(tb + (size_t)a * P, k, H, e >= 8);
-                if (c == 2) S = cmul_mi(S);                   // K_phi spectrum = -i S
-                acc = cfma(spec[a][e], S, acc);
-            }
-            v[e] = acc;
-        }
-        const int qn = next_q(q);
-        if (qn >= 0) {
-            // every read of this step's spectra precedes the TMA rewrite
-            __syncthreads();
-            fence_proxy_async();
-            issue(qn);
-        }
-        fft_any<false, LC>(v, L, T, t, xb, tw);
-        C *o = oh + (size_t)(b * 3 + c) * N * nr;
-        const uint64_t pl = l2_evict_last();
-#pragma unroll
-        for (int e = 0; e < 8; ++e) st_hint(o + blk(m, t + T * e, nr), v[e], pl);   // rows 0..nr-1 only
-        q = qn;
-    }
-}
-
 template <typename R, int NS, int LC>
 __global__ void __launch_bounds__(cols_max_threads(NS, sizeof(R) == 8, LC), cols_min_blocks(NS, sizeof(R) == 8, LC))
 k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr_rt,
@@ -758,7 +666,7 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
         return;
     }
     if constexpr (PAIR) {
-        cols_pair_steps<R, LC, NS>(sh, tab, oh, nr, N, outmask, tw, flag, xb, tb, bar, m, discard);
+        cols_pair_steps<R, LC, NS>(sh, tab, oh, nr, N, outmask, tw, flag, xb, tb, bar, m, discard, RegEngine{});
         return;
     }
     C *sspec = tb + (size_t)NS * 3 * P;           // NS == 2: source spectra in shared memory

@@ -251,4 +251,69 @@ __device__ __forceinline__ void tmem_ld8c(uint32_t taddr, float2 (&v)[8])
                  : "memory");
 }
 
+// ----------------------------------------------- tcgen05 matrix products
+// Shared-memory matrix descriptor (no swizzle): start address, the byte
+// offset between core matrices adjacent along K (lbo) and along M / N (sbo),
+// each encoded >> 4; bits 46..48 hold the fixed value 0b001.  A core matrix is
+// 8 rows of 16 bytes stored contiguously (rows 16 bytes apart).
+__device__ __forceinline__ uint64_t umma_sdesc(unsigned smem_addr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((smem_addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of a dense kind::f16 / kind::tf32 product with an
+// FP32 accumulator, A and B K-major: ab = 0 F16, 1 BF16 (kind::f16), 2 TF32.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N, uint32_t ab)
+{
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// D[tmem] (+)= A[tmem] B[smem]; issued by one thread.
+template <bool TF32>
+__device__ __forceinline__ void umma_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    if constexpr (TF32)
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+                     "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+                     : "memory");
+    else
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+                     "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+                     : "memory");
+}
+// One arrive on the mbarrier once every product this thread issued before
+// it has completed.
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 16 32-bit cells of this thread's lane to / from columns col .. col + 15.
+__device__ __forceinline__ void tmem_st16u(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+                 "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 32 cells (16 complex FP32 values) of this thread's lane, waited for.
+__device__ __forceinline__ void tmem_ld16c(uint32_t taddr, float2 (&v)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                 "[%32];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v[0].x), "=f"(v[0].y), "=f"(v[1].x), "=f"(v[1].y), "=f"(v[2].x), "=f"(v[2].y),
+                   "=f"(v[3].x), "=f"(v[3].y), "=f"(v[4].x), "=f"(v[4].y), "=f"(v[5].x), "=f"(v[5].y),
+                   "=f"(v[6].x), "=f"(v[6].y), "=f"(v[7].x), "=f"(v[7].y), "=f"(v[8].x), "=f"(v[8].y),
+                   "=f"(v[9].x), "=f"(v[9].y), "=f"(v[10].x), "=f"(v[10].y), "=f"(v[11].x), "=f"(v[11].y),
+                   "=f"(v[12].x), "=f"(v[12].y), "=f"(v[13].x), "=f"(v[13].y), "=f"(v[14].x), "=f"(v[14].y),
+                   "=f"(v[15].x), "=f"(v[15].y)
+                 : "r"(taddr)
+                 : "memory");
+}
+
 }  // namespace sg

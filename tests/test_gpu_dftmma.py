@@ -89,14 +89,48 @@ def test_fp16x3_full_size():
         assert e2 <= TOL32[0] and em <= TOL32[1], (k, e2, em)
 
 
+@pytest.mark.parametrize("engine", ["tc_bf16x3", "tc_tf32x3"])
+def test_tcgen05_split_engines_meet_fp32_tolerance(disc_1024, engine):
+    """tcgen05 engines (each radix-16 DFT one tensor-core product per
+    128-butterfly tile: operands in tensor and shared memory, FP32
+    accumulators in tensor memory; BF16 or TF32 hi + lo operands, three
+    products): the FP32 tolerance against the FP64 oracle at 1024 x 2048
+    (column length 2048: two radix-16 stages on the tensor cores)."""
+    d, ref = disc_1024
+    err = errors(solve(d, engine), ref)
+    for k, (e2, em) in err.items():
+        assert e2 <= TOL32[0] and em <= TOL32[1], (engine, k, e2, em)
+
+
+def test_tcgen05_single_product_is_worse(disc_1024):
+    """One BF16 product on the tcgen05 path is orders of magnitude less
+    accurate than the split engines: what the hi + lo split recovers."""
+    d, ref = disc_1024
+    split = max(e2 for e2, _ in errors(solve(d, "tc_bf16x3"), ref).values())
+    single = max(e2 for e2, _ in errors(solve(d, "tc_bf16"), ref).values())
+    assert single > 10 * split, (single, split)
+
+
+@pytest.mark.parametrize("engine", ["tc_bf16x3", "tc_tf32x3"])
+def test_tcgen05_full_size(engine):
+    """2048 x 4096 (column length 4096: all three radix-16 stages on the
+    tensor cores, two 128-butterfly tiles per product)."""
+    d = rounded(inputs.lognormal_gas(2048, 4096))
+    ref = oracle.fft64(oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out), d.sigma_g, h_g=d.h_g, G=d.G)
+    err = errors(solve(d, engine), ref)
+    for k, (e2, em) in err.items():
+        assert e2 <= TOL32[0] and em <= TOL32[1], (engine, k, e2, em)
+
+
 def test_engine_argument_checks():
     from paper_2506_10812_gb300 import Plan
     dev = torch.device("cuda:0")
     d = inputs.ragged_noise(512, 64)
     with Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, None, device=dev) as plan:
-        with pytest.raises(N.SgError) as ei:
-            plan.set_column_engine("dft_fp16x3")             # nr = 512
-        assert ei.value.status == N.SG_ERR_UNSUPPORTED
+        for engine in ("dft_fp16x3", "tc_bf16x3"):
+            with pytest.raises(N.SgError) as ei:
+                plan.set_column_engine(engine)               # nr = 512
+            assert ei.value.status == N.SG_ERR_UNSUPPORTED
         assert plan._lib.sg_set_column_engine(plan._h, 9) == N.SG_ERR_ARG
     with Plan(1024, 64, 0.1, 5.0, 0.05, 0.01, device=dev) as plan:  # gas + dust
         with pytest.raises(N.SgError) as ei:
