@@ -17,8 +17,9 @@
 //   B: shared memory, built once per CTA for both signs (no swizzle, K-major
 //      8 x 16-byte core matrices);
 //   D: tensor memory, FP32, read back by thread j (tcgen05.ld).
-// One thread issues the products of every tile of the CTA and commits them to
-// an mbarrier; every thread waits on it (bounded), then reads its row of D.
+// The first thread of each tile issues that tile's products and commits them
+// to the tile's mbarrier; the tile's threads wait on it (bounded), then read
+// their rows of D.
 //
 // Operands are split x = hi + lo and three products are summed in FP32:
 //   MODE 1 (BF16 x3): hi = bf16(x), lo = bf16(x - hi); kind::f16, BF16 A and B,
@@ -97,7 +98,7 @@ struct TcState {
     uint32_t a_hi, a_lo, d;      // this thread's lane: A hi / lo and D columns
     uint32_t tbase;              // the CTA's tensor-memory allocation
     unsigned bsm;                // shared-memory address of the B matrices
-    uint64_t *bar;               // product-completion mbarrier
+    uint64_t *bar;               // product-completion mbarriers, one per tile
     unsigned phase;              // its next phase parity
     unsigned int *flag;
     int failed;                  // a completion wait gave up (uniform across the CTA)
@@ -141,13 +142,16 @@ template <int L, int MODE, bool FWD> struct TcDft16 {
             if constexpr (M::split) tmem_st16u(s.a_lo, lo);
         }
         tmem_wait_st();
+        // each 128-butterfly tile (4 warps) goes on its own: its rows are
+        // written, its first thread issues and commits its products, and its
+        // threads wait on its own mbarrier
+        const int tile = t >> 7;
         tmem_fence_before();
-        __syncthreads();
+        asm volatile("bar.sync %0, 128;" ::"r"(1 + tile) : "memory");
         tmem_fence_after();
-        if (t == 0 && !s.failed) {
+        if ((t & 127) == 0 && !s.failed) {
             const unsigned b0 = s.bsm + (FWD ? 0u : 2u * M::bbytes);        // hi, then lo
-#pragma unroll
-            for (int tile = 0; tile < tc_tiles(L); ++tile) {
+            {
                 const uint32_t tb = s.tbase + tile * M::tile_cols;
                 const uint32_t ah = tb, al = tb + M::aw, d = tb + 2 * M::aw;
 #pragma unroll
@@ -163,10 +167,10 @@ template <int L, int MODE, bool FWD> struct TcDft16 {
                         umma_tmem_a<M::tf32>(d, al + 8 * k, umma_sdesc(b0 + 256 * k, M::lbo, M::sbo), M::idesc, 1u);
                 }
             }
-            umma_commit(s.bar);
+            umma_commit(s.bar + tile);
         }
         bool ok = true;
-        if (!s.failed) ok = mbar_wait_bounded(s.bar, s.phase, s.flag);
+        if (!s.failed) ok = mbar_wait_bounded(s.bar + tile, s.phase, s.flag);
         s.phase ^= 1u;
         s.failed = __syncthreads_or(!ok) || s.failed;
         tmem_fence_after();
@@ -204,8 +208,8 @@ k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 
     using M = TcMode<MODE>;
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_tc);          // staged kernel spectra
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_tc + 16);    // product completion
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_tc + 32);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_tc + 16);    // product completion, one per tile
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_tc + 48);
     unsigned char *bmat = smem_tc + 1024;
     float2 *xb = reinterpret_cast<float2 *>(bmat + 4 * M::bbytes);
     float2 *tb = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(xb) +
@@ -238,7 +242,7 @@ k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 
             *reinterpret_cast<uint16_t *>(dst) = (uint16_t)(lo ? l : h);
         }
     }
-    if (t == 0) mbar_init(mbar, 1);
+    if (t < tc_tiles(L)) mbar_init(mbar + t, 1);
     fence_proxy_async();                   // the B matrices are read by the tensor cores
     tmem_fence_before();
     __syncthreads();
