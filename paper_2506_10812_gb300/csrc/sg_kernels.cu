@@ -535,113 +535,6 @@ cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nr
 
 
 // ---------------------------------------------------------- column pass
-// Column m = 0 holds the packed (m = 0, m = nphi/2) pair of real columns:
-// Z = A + i B, so P = A S0 + i B SN = ((Z + Z*(-k)) S0 + (Z - Z*(-k)) SN) / 2.
-template <typename R, int NS>
-__device__ __noinline__ void col0_path(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
-                                       cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
-                                       const cplx<R> *__restrict__ tw, cplx<R> *xb, cplx<R> *spec)
-{
-    using C = cplx<R>;
-    const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
-    const int t = threadIdx.x;
-    C v[16];
-    for (int a = 0; a < NS; ++a) {
-        const C *col = sh + (size_t)a * N * nr;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(col + blk(0, t + T * e, nr), l2_evict_first());
-#pragma unroll
-        for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
-        fft_reg<true>(v, L, T, t, xb, tw);
-#pragma unroll
-        for (int e = 0; e < 16; ++e) spec[a * L + t + T * e] = v[e];
-    }
-    __syncthreads();
-    for (int b = 0; b < NS; ++b) {
-        for (int c = 0; c < 3; ++c) {
-            if (!((outmask >> (3 * b + c)) & 1u)) continue;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int k = t + T * e;
-                C acc = mkc<C>(0, 0);
-                for (int a = 0; a < NS; ++a) {
-                    const C *t0 = tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1)) * P;
-                    const C *tn = t0 + (size_t)N * P;
-                    const C Z = spec[a * L + k];
-                    const C Zm = cconj(spec[a * L + ((L - k) & (L - 1))]);
-                    C S0 = spec_at(t0, k, H, e >= 8), SN = spec_at(tn, k, H, e >= 8);
-                    if (c == 2) {
-                        S0 = cmul_mi(S0);
-                        SN = cmul_mi(SN);
-                    }
-                    acc = cadd(acc, cscale(cadd(cmul(cadd(Z, Zm), S0), cmul(csub(Z, Zm), SN)), (R)0.5));
-                }
-                v[e] = acc;
-            }
-            fft_reg<false>(v, L, T, t, xb, tw);
-            C *o = oh + (size_t)(b * 3 + c) * N * nr;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) o[blk(0, t + T * e, nr)] = v[e];
-        }
-    }
-}
-
-// LC > 0: compile-time column length (2 nr).
-// Column 0 of a plan that stages kernel spectra per step (no shared-memory
-// source spectra): each requested (target, component) step transforms the
-// packed source columns again and pairs Z(k) with Z*(L - k) through the
-// exchange buffer.  The same terms in the same order as col0_path, so the
-// same result; for gas + dust 18 transforms instead of 8, in one CTA of the
-// first wave.
-template <typename R, int NS>
-__device__ __noinline__ void col0_recompute(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab,
-                                            cplx<R> *__restrict__ oh, int nr, int N, uint32_t outmask,
-                                            const cplx<R> *__restrict__ tw, cplx<R> *xb)
-{
-    using C = cplx<R>;
-    const int L = 2 * nr, T = L >> 4, H = nr, P = tab_pitch(nr);
-    const int t = threadIdx.x;
-    for (int q = 0; q < 3 * NS; ++q) {
-        if (!((outmask >> q) & 1u)) continue;
-        const int b = q / 3, c = q % 3;
-        C acc[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[e] = mkc<C>(0, 0);
-        for (int a = 0; a < NS; ++a) {
-            C v[16];
-            const C *col = sh + (size_t)a * N * nr;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(col + blk(0, t + T * e, nr), l2_evict_first());
-#pragma unroll
-            for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);
-            fft_reg<true>(v, L, T, t, xb, tw);
-            __syncthreads();                   // the transform's last exchange reads are done
-#pragma unroll
-            for (int e = 0; e < 16; ++e) xb[pidx(t + T * e)] = v[e];
-            __syncthreads();
-            const C *t0 = tab + ((size_t)((a * NS + b) * 3 + c) * (N + 1)) * P;
-            const C *tn = t0 + (size_t)N * P;
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int k = t + T * e;
-                const C Z = v[e];
-                const C Zm = cconj(xb[pidx((L - k) & (L - 1))]);
-                C S0 = spec_at(t0, k, H, e >= 8), SN = spec_at(tn, k, H, e >= 8);
-                if (c == 2) {
-                    S0 = cmul_mi(S0);
-                    SN = cmul_mi(SN);
-                }
-                acc[e] = cadd(acc[e], cscale(cadd(cmul(cadd(Z, Zm), S0), cmul(csub(Z, Zm), SN)), (R)0.5));
-            }
-            __syncthreads();                   // before the next transform rewrites the buffer
-        }
-        fft_reg<false>(acc, L, T, t, xb, tw);
-        C *o = oh + (size_t)(b * 3 + c) * N * nr;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) o[blk(0, t + T * e, nr)] = acc[e];
-    }
-}
-
 template <typename R, int NS, int LC>
 __global__ void __launch_bounds__(cols_max_threads(NS, sizeof(R) == 8, LC), cols_min_blocks(NS, sizeof(R) == 8, LC))
 k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> *__restrict__ oh, int nr_rt,
