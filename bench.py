@@ -166,7 +166,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash(names=("sg_kernels.cu", "sg_fft.cuh", "sg_mem.cuh")):
+def kernel_source_hash(names=("sg_kernels.cu", "sg_cols.cuh", "sg_fft.cuh", "sg_mem.cuh")):
     h = hashlib.sha256()
     for name in names:
         with open(os.path.join(ROOT, "paper_2506_10812_gb300", "csrc", name), "rb") as f:
