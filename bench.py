@@ -166,7 +166,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash(names=("sg_kernels.cu", "sg_cols.cuh", "sg_fft.cuh", "sg_mem.cuh")):
+def kernel_source_hash(names=("sg_kernels.cu", "sg_cols.cuh", "sg_cols_steps.cu", "sg_fft.cuh", "sg_mem.cuh")):
     h = hashlib.sha256()
     for name in names:
         with open(os.path.join(ROOT, "paper_2506_10812_gb300", "csrc", name), "rb") as f:
@@ -192,7 +192,8 @@ def batch_profiled_ratio(streams=False):
     """DRAM bytes per model byte of a batch step, from the committed ncu
     summary of a smaller batch on the same sources: the persistent kernel's,
     or (streams) the sum over the per-disc launch chains of one step."""
-    path, names = ((BATCH_STREAMS_PROFILE, ("sg_batch.cu", "sg_kernels.cu", "sg_fft.cuh", "sg_mem.cuh")) if streams
+    path, names = ((BATCH_STREAMS_PROFILE, ("sg_batch.cu", "sg_kernels.cu", "sg_rows.cu", "sg_cols.cuh",
+                                            "sg_cols_steps.cu", "sg_fft.cuh", "sg_mem.cuh")) if streams
                    else (BATCH_PROFILE, ("sg_batch.cu", "sg_fft.cuh", "sg_mem.cuh")))
     try:
         txt = open(path).read()
@@ -542,6 +543,16 @@ def run_batch(args):
     tune_ms = (time.perf_counter() - t0) * 1e3
     cfg = batch.config()
     tried = batch.tune_results()
+    tile_trials = batch.tile_trials()
+    # the other engine's fastest candidate, timed beside the tuned one
+    other = None
+    if args.batch_config == "auto":
+        rest = [(c, m) for c, m in tried if ("streams" in c) != bool(cfg.get("streams", 0))]
+        if rest:
+            c, _ = min(rest, key=lambda x: x[1])
+            other = (Batch(plans, sg, sd, outs, streams=c["streams"]) if "streams" in c else
+                     Batch(plans, sg, sd, outs, threads=c["threads"], ctas_per_sm=c["ctas_per_sm"],
+                           order=c["order"], specialize=c["specialize"]))
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def py_loop():
@@ -571,6 +582,10 @@ def run_batch(args):
     K, W = args.steps, args.warmup
     ms_graph, clk = timed(batch.solve, K, W, ClockSampler(dev.index))
     batch.sync()
+    ms_other = None
+    if other is not None:
+        ms_other, _ = timed(other.solve, K, W)
+        other.sync()
     if args.no_loop:
         ms_loop_c = ms_loop_py = float("nan")
     else:
@@ -587,6 +602,26 @@ def run_batch(args):
               if streams else "one persistent launch per step from a CUDA graph")
     from collections import Counter
     shapes = Counter(f"{d.nr}x{d.nphi}" for d in discs)
+
+    def engine_line(c, ms):
+        st = c.get("streams", 0)
+        r = batch_profiled_ratio(streams=bool(st))
+        a = model / (ms * 1e-3) / 1e9
+        return {"config": c, "ms_per_step": ms, "value": cells / (ms * 1e-3),
+                "roofline": {"bound": "hbm", "achieved": round(a, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(a / peak, 4), "traffic": None if r is None else round(r * model)}}
+
+    engines = {("streams" if cfg.get("streams", 0) else "persistent"): engine_line(cfg, ms_graph)}
+    if other is not None:
+        oc = other.config()
+        engines["streams" if oc.get("streams", 0) else "persistent"] = engine_line(oc, ms_other)
+    tiles_by_shape = {}
+    for t in tile_trials:
+        key = f"{t['nr']}x{t['nphi']}" + ("+dust" if t["nsrc"] == 2 else "")
+        e = tiles_by_shape.setdefault(key, {"disc": t["disc"], "candidates": []})
+        e["candidates"].append(dict(t["tiles"], ms=round(t["ms"], 4)))
+        if t["chosen"]:
+            e["chosen"] = t["tiles"]
     result = {"metric": METRIC, "value": cells / (ms_graph * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": K,
               "warmup": W, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic (64 seeded log-normal gas + dust discs)",
@@ -598,6 +633,8 @@ def run_batch(args):
                          "kernel_spectra": "built once per plan, outside the timed steps"},
               "batch_config": cfg,
               "autotune_candidates": [dict(c, ms=round(m, 4)) for c, m in tried],
+              "engines": engines,
+              "tile_trials": tiles_by_shape,
               "roofline": {"bound": "hbm",
                            "kernel": (f"per-disc solve chains on {streams} streams (whole step)" if streams
                                       else "k_batch (persistent, whole step)"),
@@ -617,6 +654,8 @@ def run_batch(args):
               "gpu_launches": K * (cfg["tasks"] if streams else 1), "clocks": clk}
     print(json.dumps(result), flush=True)
     batch.close()
+    if other is not None:
+        other.close()
     for p in plans:
         p.close()
 

@@ -219,6 +219,42 @@ sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, const void 
                             void *phi_d, void *gr_d, void *gphi_d, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Launch tiles of an FFT plan's kernels.  The paper fixes no GPU work
+ * decomposition (its FFT convolution, Sec. 5.2, runs on CPU cores); these
+ * choose how the solve's three kernels split the grid, and do not change
+ * what is computed:
+ *   rows_fwd, rows_inv  grid rows per CTA (2 or 4) of the forward and the
+ *                       inverse row transforms where those move their tiles
+ *                       by tensor copies (FP32 plans with nphi in
+ *                       {512, 1024, 2048, 4096} and nr % 4 == 0); other plans
+ *                       record the value and run their own row kernels.
+ *   cols_staging        SG_COLS_STAGE_ALL: the column pass stages every
+ *                       requested kernel-spectrum table of a target in shared
+ *                       memory at once; SG_COLS_STAGE_STEP: one (target,
+ *                       component) step at a time while the source spectra
+ *                       stay in registers (FP32 plans only).
+ * Defaults: rows_fwd 4, rows_inv 2; per-step staging for FP32 gas + dust and
+ * FP32 gas-only plans with nr = 2048, all at once otherwise.  Every tile
+ * set performs the same operations on every element, but each kernel
+ * variant is compiled separately and fuses multiply-adds in its own way, so
+ * solves with different tiles agree to FP32 rounding (relative L2 ~1e-7),
+ * not bit for bit; equal tiles give equal bits.  sg_set_tiles re-encodes the
+ * plan's tensor maps on the host (no device work, no allocation); solves
+ * already enqueued keep the tiles they were launched with.  Errors:
+ * SG_ERR_ARG (NULL, a value outside the lists above), SG_ERR_UNSUPPORTED
+ * (a direct-method plan, per-step staging of an FP64 plan, a staging whose
+ * shared memory exceeds the device's per-block limit).  Batches' stream
+ * engine and sg_batch_solve_loop launch with each plan's tiles.            */
+enum { SG_COLS_STAGE_ALL = 0, SG_COLS_STAGE_STEP = 1 };
+typedef struct {
+    int32_t rows_fwd;
+    int32_t rows_inv;
+    int32_t cols_staging;
+} sg_tiles;
+sg_status sg_get_tiles(const sg_plan *plan, sg_tiles *tiles);
+sg_status sg_set_tiles(sg_plan *plan, const sg_tiles *tiles);
+
+/* ------------------------------------------------------------------------
  * Batches of independent discs.  The paper evolves one disc per run and
  * builds its kernel once per run (Sec. 5.2); a batch binds many FFT plans
  * (uneven grids, gas-only or gas + dust, one dtype, one device) and their
@@ -257,9 +293,13 @@ typedef struct {
                               for (rows of nphi 2048 and 4096, columns of 2 nr =
                               1024, 2048, 4096) use compile-time kernels; other
                               lengths and FP64 stay generic                      */
-    int32_t autotune;      /* 1: time every (specialize, threads, ctas_per_sm,
-                              order) candidate on the bound buffers at create and
-                              keep the fastest; those four fields are ignored   */
+    int32_t autotune;      /* 1: at create, on the bound buffers, first give each
+                              plan shape its fastest launch tiles
+                              (sg_batch_tile_trials), then time every
+                              (specialize, threads, ctas_per_sm, order)
+                              candidate of the persistent engine and every
+                              stream count of the stream engine, and keep the
+                              fastest; those five fields are ignored          */
     uint32_t flags;        /* SG_CHECK_FINITE, SG_BATCH_HOST_GATE                   */
     double timeout_ms;     /* bound of each device-side wait (0: 2000 ms)          */
     int32_t streams;       /* 0: the persistent kernel; 1..64: the per-disc launch
@@ -317,11 +357,30 @@ sg_status sg_batch_sync(sg_batch *batch, void *stream);
 sg_status sg_batch_config(const sg_batch *batch, sg_batch_opts *opts, int32_t *grid,
                           int32_t *ntasks, float *tuned_ms);
 
-/* The autotuner's candidates in the order they were timed: writes up to
- * `max` configurations to cfgs and their median times per solve (ms) to ms
+/* The autotuner's engine candidates in the order they were timed (the tile
+ * trials before them: sg_batch_tile_trials): writes up to `max`
+ * configurations to cfgs and their median times per solve (ms) to ms
  * (either may be NULL) and returns how many were timed (0 without
  * autotune; -1 for a NULL batch).                                         */
 int32_t sg_batch_tune_results(const sg_batch *batch, int32_t max, sg_batch_opts *cfgs, float *ms);
+
+/* The autotuner's launch-tile trials (sg_tiles), in the order they were
+ * timed: per plan shape (nr, nphi, nsrc), every candidate tile set timed on
+ * the first disc of that shape with sg_solve alone (median ms of 5 solves
+ * after 2 warm-ups); `chosen` marks the set every disc of the shape was then
+ * given (sg_set_tiles on the caller's plans, kept after the batch is
+ * destroyed).  The stream engine and sg_batch_solve_loop launch with those
+ * tiles; the persistent kernel has its own decomposition (threads,
+ * ctas_per_sm).  Writes up to `max` trials to `out` (may be NULL) and returns
+ * how many were timed (0 without autotune; -1 for a NULL batch).          */
+typedef struct {
+    int32_t disc;
+    int32_t nr, nphi, nsrc;
+    sg_tiles tiles;
+    float ms;
+    int32_t chosen;
+} sg_tile_trial;
+int32_t sg_batch_tile_trials(const sg_batch *batch, int32_t max, sg_tile_trial *out);
 
 /* Release the batch (not its plans or buffers).  Synchronises the device. */
 void sg_batch_destroy(sg_batch *batch);

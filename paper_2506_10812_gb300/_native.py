@@ -27,8 +27,8 @@ ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf1
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
-           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_set_column_engine", "sg_batch_create", "sg_batch_solve",
-           "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_tune_results", "sg_batch_destroy",
+           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_set_column_engine", "sg_get_tiles", "sg_set_tiles", "sg_batch_create", "sg_batch_solve",
+           "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_tune_results", "sg_batch_tile_trials", "sg_batch_destroy",
            "sg_batch_last_error", "sg_nn_gemm", "sg_nn_spec_combine", "sg_nn_spec_combine_bwd", "sg_nn_modemix",
            "sg_nn_modemix_bwd", "sg_nn_act", "sg_nn_act_bwd", "sg_nn_colsum", "sg_nn_rel_l2", "sg_nn_adam", "sg_nn_cast",
            "sg_nn_transpose", "sg_nn_fields", "sg_nn_pack_inputs", "sg_nn_pack_targets", "sg_destroy", "sg_status_string", "sg_last_error")
@@ -47,6 +47,18 @@ class SgBatchOpts(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("specialize", ctypes.c_int32), ("autotune", ctypes.c_int32), ("flags", ctypes.c_uint32), ("timeout_ms", ctypes.c_double),
                 ("streams", ctypes.c_int32)]
+
+
+class SgTiles(ctypes.Structure):
+    _fields_ = [("rows_fwd", ctypes.c_int32), ("rows_inv", ctypes.c_int32), ("cols_staging", ctypes.c_int32)]
+
+
+class SgTileTrial(ctypes.Structure):
+    _fields_ = [("disc", ctypes.c_int32), ("nr", ctypes.c_int32), ("nphi", ctypes.c_int32),
+                ("nsrc", ctypes.c_int32), ("tiles", SgTiles), ("ms", ctypes.c_float), ("chosen", ctypes.c_int32)]
+
+
+COLS_STAGING = {"all": 0, "step": 1}
 
 
 class SgError(RuntimeError):
@@ -110,6 +122,12 @@ def load() -> ctypes.CDLL:
     lib.sg_batch_last_error.restype = ctypes.c_char_p
     lib.sg_set_column_engine.argtypes = [vp, i32]
     lib.sg_set_column_engine.restype = st
+    lib.sg_get_tiles.argtypes = [vp, ctypes.POINTER(SgTiles)]
+    lib.sg_get_tiles.restype = st
+    lib.sg_set_tiles.argtypes = [vp, ctypes.POINTER(SgTiles)]
+    lib.sg_set_tiles.restype = st
+    lib.sg_batch_tile_trials.argtypes = [vp, i32, ctypes.POINTER(SgTileTrial)]
+    lib.sg_batch_tile_trials.restype = i32
     i64, f32 = ctypes.c_int64, ctypes.c_float
     nn = {
         "sg_nn_gemm": [i32, i32, i32, i32, f32, vp, i32, i64, i32, vp, i32, i64, f32, vp, i32, i64, vp, vp, vp],

@@ -104,6 +104,19 @@ class Batch:
                  {"threads": c.threads, "ctas_per_sm": c.ctas_per_sm, "order": ("pipelined", "staged")[c.order],
                   "specialize": bool(c.specialize)}, float(m)) for c, m in zip(cfgs[:n], ms[:n])]
 
+    def tile_trials(self):
+        """[trial dict] of every launch-tile candidate the autotuner timed:
+        disc, shape (nr, nphi, nsrc), tiles, median ms of one solve of that
+        disc, and whether the shape's discs now use it."""
+        n = self._lib.sg_batch_tile_trials(self._h, 0, None)
+        out = (N.SgTileTrial * max(n, 1))()
+        self._lib.sg_batch_tile_trials(self._h, n, out)
+        names = {v: k for k, v in N.COLS_STAGING.items()}
+        return [{"disc": t.disc, "nr": t.nr, "nphi": t.nphi, "nsrc": t.nsrc,
+                 "tiles": {"rows_fwd": t.tiles.rows_fwd, "rows_inv": t.tiles.rows_inv,
+                           "cols_staging": names[t.tiles.cols_staging]},
+                 "ms": float(t.ms), "chosen": bool(t.chosen)} for t in out[:n]]
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.sg_batch_destroy(self._h)

@@ -164,6 +164,16 @@ constexpr double kAlpha = 1.0;
 
 // Build the packed kernel spectra of every ordered fluid pair (App. C
 // lattice kernels, Sec. 5.2 precomputation).
+// The row transforms' tensor maps of sh and oh, boxes of the plan's tiles.
+void encode_maps(sg_plan *pl)
+{
+    pl->tm_rows = rows_tma_eligible(pl->p.nr, pl->p.nphi, pl->f64) &&
+                  encode_row_map(&pl->tm_sh, pl->sh, pl->p.nr, (long long)pl->nsrc * pl->N, pl->rows_fwd) ==
+                      cudaSuccess &&
+                  encode_row_map(&pl->tm_oh, pl->oh, pl->p.nr, (long long)pl->nsrc * 3 * pl->N, pl->rows_inv) ==
+                      cudaSuccess;
+}
+
 sg_status build_tables(sg_plan *pl, cudaStream_t s)
 {
     const int nr = pl->p.nr, nphi = pl->p.nphi, L = pl->L, N = pl->N;
@@ -233,7 +243,7 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
     if (pl->p.method == SG_METHOD_FFT) {
         e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row,
                                pl->twp_row, (const R *)pl->rcen, true, s, 0, -1, pl->tm_rows ? &pl->tm_sh : nullptr,
-                               sflag);
+                               sflag, pl->rows_fwd);
         if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
         if (ev) cudaEventRecord(pl->ev[1], s);
         e = pl->engine >= SG_ENGINE_TC_BF16X3
@@ -241,7 +251,7 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
             : pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
                                            sflag, s)
                          : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, sflag, s,
-                                        0, !ev, true);
+                                          0, !ev, true, pl->cols_staging);
         if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
         if (ev) cudaEventRecord(pl->ev[2], s);
         RowOut ro{};
@@ -253,7 +263,7 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
             ++ro.n;
         }
         e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, 0, -1,
-                               pl->tm_rows ? &pl->tm_oh : nullptr, sflag, !ev);
+                               pl->tm_rows ? &pl->tm_oh : nullptr, sflag, !ev, pl->rows_inv);
         if (e != cudaSuccess) return cuda_fail(pl, e, "inverse row transform");
         if (ev) cudaEventRecord(pl->ev[3], s);
     } else {
@@ -337,7 +347,8 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ein[k], 0);
         if (e == cudaSuccess)
             e = launch_rows_fwd<R>(dsg, dsd, pl->nsrc, pl->sh, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen,
-                                   true, s, k * rows_in, rows_in, pl->tm_rows ? &pl->tm_sh : nullptr, pl->flag);
+                                   true, s, k * rows_in, rows_in, pl->tm_rows ? &pl->tm_sh : nullptr, pl->flag,
+                                   pl->rows_fwd);
     }
     if (e != cudaSuccess) return cuda_fail(pl, e, "pipelined input and row transform");
     if (!mask) return cuda_fail(pl, cudaStreamSynchronize(s), "solve");
@@ -346,7 +357,7 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
         : pl->engine ? launch_cols_mma(pl->engine, pl->sh, pl->tab, pl->oh, nr, nphi, mask, pl->twp_col, pl->atab,
                                        pl->flag, s)
                      : launch_cols<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, pl->twp_col, pl->flag, s, 0,
-                                    true, true);
+                                      true, true, pl->cols_staging);
     if (e != cudaSuccess) return cuda_fail(pl, e, "column pass");
     RowOut ro{};
     for (int q = 0; q < 6; ++q) {
@@ -359,7 +370,7 @@ sg_status solve_host_fft(sg_plan *pl, const void *hsg, const void *hsd, void *co
     for (int k = 0; k < nch && e == cudaSuccess; ++k) {
         // chunk 0 follows the column pass directly: a programmatic dependent of it
         e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, k * rows,
-                               rows, pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag, k == 0);
+                               rows, pl->tm_rows ? &pl->tm_oh : nullptr, pl->flag, k == 0, pl->rows_inv);
         if (k != 0 && k != nch - 1) continue;
         // copy group: chunk 0, then chunks 1 .. nch-1
         const int k0 = k == 0 ? 0 : 1;
@@ -474,11 +485,7 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
                "kernel spectra");
         SG_TRY(cudaMalloc(&pl->sh, (size_t)pl->nsrc * pl->N * p->nr * cbytes), "scratch");
         SG_TRY(cudaMalloc(&pl->oh, (size_t)pl->nsrc * 3 * pl->N * p->nr * cbytes), "scratch");
-        if (rows_tma_eligible(p->nr, p->nphi, pl->f64))
-            pl->tm_rows = encode_row_map(&pl->tm_sh, pl->sh, p->nr, (long long)pl->nsrc * pl->N,
-                                         rows_tma_fwd_rows()) == cudaSuccess &&
-                          encode_row_map(&pl->tm_oh, pl->oh, p->nr, (long long)pl->nsrc * 3 * pl->N,
-                                         rows_tma_inv_rows()) == cudaSuccess;
+        encode_maps(pl);
         sg_status st = build_tables(pl, s);
         if (st != SG_OK) {
             fprintf(stderr, "sg_plan_create: %s\n", pl->err);
@@ -695,6 +702,40 @@ sg_status sg_set_column_engine(sg_plan *pl, int32_t engine)
     if (e == cudaSuccess) e = cudaMemcpy(pl->atab, h, sizeof(h), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(pl, e, "fragment table");
     pl->engine = engine;
+    return SG_OK;
+}
+
+sg_status sg_get_tiles(const sg_plan *pl, sg_tiles *t)
+{
+    if (!pl || !t) return SG_ERR_ARG;
+    t->rows_fwd = pl->rows_fwd;
+    t->rows_inv = pl->rows_inv;
+    t->cols_staging = cols_staging_steps(pl->p.nr, pl->nsrc, pl->f64, pl->cols_staging) ? SG_COLS_STAGE_STEP
+                                                                                          : SG_COLS_STAGE_ALL;
+    return SG_OK;
+}
+
+sg_status sg_set_tiles(sg_plan *pl, const sg_tiles *t)
+{
+    if (!pl) return SG_ERR_ARG;
+    if (!t) return fail(pl, SG_ERR_ARG, "tiles is NULL");
+    if ((t->rows_fwd != 2 && t->rows_fwd != 4) || (t->rows_inv != 2 && t->rows_inv != 4))
+        return fail(pl, SG_ERR_ARG, "rows per CTA must be 2 or 4");
+    if (t->cols_staging != SG_COLS_STAGE_ALL && t->cols_staging != SG_COLS_STAGE_STEP)
+        return fail(pl, SG_ERR_ARG, "unknown column staging %d", t->cols_staging);
+    if (pl->p.method != SG_METHOD_FFT) return fail(pl, SG_ERR_UNSUPPORTED, "tiles apply to FFT plans");
+    if (pl->f64 && t->cols_staging == SG_COLS_STAGE_STEP)
+        return fail(pl, SG_ERR_UNSUPPORTED, "per-step column staging is FP32 only");
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
+    if (e != cudaSuccess) return cuda_fail(pl, e, "device attribute");
+    if (col_smem_bytes(pl->p.nr, pl->nsrc, pl->f64, t->cols_staging) > (size_t)optin)
+        return fail(pl, SG_ERR_UNSUPPORTED, "this column staging needs %zu bytes of shared memory per block",
+                    col_smem_bytes(pl->p.nr, pl->nsrc, pl->f64, t->cols_staging));
+    pl->rows_fwd = t->rows_fwd;
+    pl->rows_inv = t->rows_inv;
+    pl->cols_staging = t->cols_staging;
+    encode_maps(pl);
     return SG_OK;
 }
 

@@ -665,6 +665,7 @@ struct sg_batch {
     float tuned_ms = 0.f;
     std::vector<sg_batch_opts> tried;    // autotune candidates and their times
     std::vector<float> tried_ms;
+    std::vector<sg_tile_trial> tile_trials;   // autotune: launch tiles timed per plan shape
     void *discs = nullptr;               // BatchDisc<R>[n]
     int4 *tasks = nullptr;
     size_t tasks_cap = 0;
@@ -994,6 +995,94 @@ sg_status time_config(sg_batch *b, cudaStream_t s, int reps, float *ms)
     return SG_OK;
 }
 
+// Launch tiles per plan shape (nr, nphi, nsrc): every candidate (rows per CTA
+// of the tensor-copy row transforms, column staging) timed on the first disc
+// of the shape with sg_solve's launch chain alone, median of `reps` solves
+// after 2 warm-ups; every disc of the shape then takes the fastest.  Shapes
+// whose row transforms do not use tensor copies vary the staging only.
+sg_status tune_tiles(sg_batch *b, cudaStream_t s, int reps)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return bcuda(b, e, "tile trials");
+    }
+    const bool finite = (b->flags & SG_CHECK_FINITE) != 0;
+    sg_status st = SG_OK;
+    for (int k = 0; k < b->n && st == SG_OK; ++k) {
+        sg_plan *pl = b->plans[k];
+        auto same = [&](const sg_plan *q) {
+            return q->p.nr == pl->p.nr && q->p.nphi == pl->p.nphi && q->nsrc == pl->nsrc;
+        };
+        bool seen = false;
+        for (int j = 0; j < k && !seen; ++j) seen = same(b->plans[j]);
+        if (seen) continue;
+        sg_tiles t0{};
+        sg_get_tiles(pl, &t0);
+        const bool rows = rows_tma_eligible(pl->p.nr, pl->p.nphi, pl->f64);
+        const size_t first = b->tile_trials.size();
+        float best = 0.f;
+        sg_tiles bt = t0;
+        for (int stg = 0; stg <= (pl->f64 ? 0 : 1) && st == SG_OK; ++stg)
+            for (int rf : {2, 4})
+                for (int ri : {2, 4}) {
+                    if (st != SG_OK) break;
+                    if (!rows && (rf != t0.rows_fwd || ri != t0.rows_inv)) continue;
+                    const sg_tiles t{rf, ri, stg};
+                    const sg_status ts = sg_set_tiles(pl, &t);
+                    if (ts == SG_ERR_UNSUPPORTED) continue;   // staging over the shared-memory limit
+                    if (ts != SG_OK) {
+                        st = bfail(b, ts, "disc %d: %s", k, sg_last_error(pl));
+                        break;
+                    }
+                    std::vector<float> ms;
+                    for (int r = 0; r < reps + 2 && st == SG_OK; ++r) {
+                        e = cudaEventRecord(e0, s);
+                        if (e == cudaSuccess) {
+                            st = solve_into(pl, b->sg[k], b->sd[k], b->outs.data() + 6 * (size_t)k, s, b->flag,
+                                            finite);
+                            if (st != SG_OK) st = bfail(b, st, "disc %d: %s", k, sg_last_error(pl));
+                        }
+                        if (st == SG_OK && e == cudaSuccess) e = cudaEventRecord(e1, s);
+                        if (st == SG_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+                        float x = 0.f;
+                        if (st == SG_OK && e == cudaSuccess && r >= 2 && cudaEventElapsedTime(&x, e0, e1) == cudaSuccess)
+                            ms.push_back(x);
+                        if (e != cudaSuccess) st = bcuda(b, e, "tile trial");
+                    }
+                    if (st != SG_OK) break;
+                    std::sort(ms.begin(), ms.end());
+                    const float med = ms.empty() ? 0.f : ms[ms.size() / 2];
+                    b->tile_trials.push_back(sg_tile_trial{k, pl->p.nr, pl->p.nphi, pl->nsrc, t, med, 0});
+                    if (b->tile_trials.size() == first + 1 || med < best) {
+                        best = med;
+                        bt = t;
+                    }
+                }
+        if (st != SG_OK) break;
+        for (size_t i = first; i < b->tile_trials.size(); ++i) {
+            const sg_tiles &t = b->tile_trials[i].tiles;
+            b->tile_trials[i].chosen = t.rows_fwd == bt.rows_fwd && t.rows_inv == bt.rows_inv &&
+                                       t.cols_staging == bt.cols_staging;
+        }
+        for (int j = k; j < b->n && st == SG_OK; ++j)
+            if (same(b->plans[j])) {
+                const sg_status ts = sg_set_tiles(b->plans[j], &bt);
+                if (ts != SG_OK) st = bfail(b, ts, "disc %d: %s", j, sg_last_error(b->plans[j]));
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SG_OK) return st;
+    unsigned f = 0;
+    e = cudaMemcpy(&f, b->flag, sizeof(f), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bcuda(b, e, "tile trials");
+    if (f & 6u) return bfail(b, SG_ERR_TIMEOUT, "a device wait gave up while timing tiles");
+    return SG_OK;
+}
+
 void batch_free(sg_batch *b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1092,6 +1181,9 @@ sg_status sg_batch_create(sg_batch **out, sg_plan *const *plans, int32_t n, cons
 
     sg_status st;
     if (o.autotune && !(o.flags & SG_BATCH_HOST_GATE)) {
+        // the plans' launch tiles first: the stream engine's chains use them
+        st = tune_tiles(b, (cudaStream_t)stream, 5);
+        if (st != SG_OK) return bad(st);
         float best = 0.f;
         sg_batch_opts bc{};
         bool have = false;
@@ -1221,6 +1313,14 @@ int32_t sg_batch_tune_results(const sg_batch *b, int32_t max, sg_batch_opts *cfg
         if (cfgs) cfgs[i] = b->tried[i];
         if (ms) ms[i] = b->tried_ms[i];
     }
+    return n;
+}
+
+int32_t sg_batch_tile_trials(const sg_batch *b, int32_t max, sg_tile_trial *out)
+{
+    if (!b) return -1;
+    const int n = (int)b->tile_trials.size();
+    for (int i = 0; i < n && i < max && out; ++i) out[i] = b->tile_trials[i];
     return n;
 }
 

@@ -21,11 +21,17 @@ namespace sg {
 // chunks; both the forward and the inverse use the same shared-memory size.
 int row_rpc(int nphi, bool f64);
 size_t row_smem_bytes(int nphi, int rpc, bool f64);
-size_t col_smem_bytes(int nr, int nsrc, bool f64);
+// Column pass: shared memory per CTA and whether kernel spectra are staged
+// per (target, component) step; staging < 0 is the plan default, 0 all
+// tables at once, 1 per step (FP32 only; FP64 always all at once).
+size_t col_smem_bytes(int nr, int nsrc, bool f64, int staging = -1);
+bool cols_staging_steps(int nr, int nsrc, bool f64, int staging);
 size_t tabcol_smem_bytes(int L, bool f64);
 // complex slots per stored kernel-spectrum column
 __host__ __device__ inline int tab_pitch(int nr) { return nr + 2; }
-cudaError_t set_smem_limits(int max_optin);
+cudaError_t set_cols_steps_smem_limits(int max_optin);   // the per-step column kernels
+cudaError_t set_smem_limits(int max_optin);       // every kernel (calls set_row_smem_limits)
+cudaError_t set_row_smem_limits(int max_optin);   // the row transforms (sg_rows.cu)
 
 // Kernel-table evaluation (App. C lattice), one ordered pair (source aspect
 // ratio ha, target hb), all three components times scale * e^{alpha Delta},
@@ -41,24 +47,21 @@ cudaError_t launch_tab_eval(int nr, int nphi, double du, double ha, double hb, d
 // (slot m = 0 packs the real m = 0 and m = nphi/2 coefficients).
 // row0, nrows_run: transform only rows row0 .. row0 + nrows_run - 1 (multiples
 // of row_rpc; nrows_run < 0: to the end); nrows stays the row stride.
-// tm: the tensor map of xh (encode_row_map over nsrc nphi/2 columns); with
-// it, FP32 rows of the hot lengths (rows_tma_eligible) store their spectrum
-// tiles by bulk tensor copies (bit 2 of *tflag when a staged copy never
-// completed).
+// tm: the tensor map of xh (encode_row_map over nsrc nphi/2 columns, box of
+// tile_rows rows); with it, FP32 rows of the hot lengths (rows_tma_eligible)
+// store their spectrum tiles by bulk tensor copies, tile_rows (2 or 4) rows
+// per CTA (bit 2 of *tflag when a staged copy never completed).
 template <typename R>
 cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nrows, int nphi,
                             const void *tw_row, const void *twp_row, const R *rscale, bool dc, cudaStream_t s,
                             int row0 = 0, int nrows_run = -1, const CUtensorMap *tm = nullptr,
-                            unsigned int *tflag = nullptr);
+                            unsigned int *tflag = nullptr, int tile_rows = 4);
 
 // 2-D tensor map of a [ncols][nr] complex FP32 intermediate for the
 // tensor-copy row transforms; rows_tma_eligible: the sizes they take.
-// `rows`: rows per CTA of the kernel that uses the map (rows_tma_fwd_rows for
-// the row spectra, rows_tma_inv_rows for the column output).
+// `rows`: rows per CTA of the kernel that uses the map (the plan's tiles).
 cudaError_t encode_row_map(CUtensorMap *m, void *base, int nr, long long ncols, int rows);
 bool rows_tma_eligible(int nr, int nphi, bool f64);
-int rows_tma_fwd_rows();
-int rows_tma_inv_rows();
 
 // Column pass of the solve: forward padded FFT of every source column,
 // products with the packed kernel spectra, inverse FFT of every requested
@@ -69,10 +72,15 @@ int rows_tma_inv_rows();
 // spectrum copies overlap that kernel's last CTAs).  discard: the row spectra
 // are dead once read, so each column's L2 lines are discarded after its
 // forward transform (never written back; the caller reads sh no more).
+// staging: kernel-spectrum staging (col_smem_bytes).
 template <typename R>
 cudaError_t launch_cols(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc,
                         uint32_t outmask, const void *tw_col, unsigned int *flag, cudaStream_t s, int ncols = 0,
-                        bool pdl = false, bool discard = false);
+                        bool pdl = false, bool discard = false, int staging = -1);
+// the per-step (FP32) column kernel of a plan shape, L = 2 nr
+using ColsKernelF32 = void (*)(const float2 *, const float2 *, float2 *, int, int, uint32_t, const float2 *,
+                               unsigned int *, int);
+ColsKernelF32 cols_kernel_steps(int nsrc, int L);
 
 // Column pass with tensor-core DFT stages (sg_dftmma.cu): FP32 gas-only
 // plans with 2 nr in {2048, 4096}; engine 1..4 as SG_ENGINE_DFT_*; atab
@@ -106,14 +114,14 @@ struct RowOut {
 // (accelerations divided by r_i, undoing the radial source scaling; finite
 // check into *flag bit 1 when flag != NULL).
 // tm: the tensor map of oh (all nsrc * 3 spectra); with it, FP32 rows of the
-// hot lengths load their tiles by bulk tensor copies (bit 2 of *tflag when a
-// copy never completed).  pdl: programmatic dependent launch on the column
-// pass before it.
+// hot lengths load their tiles by bulk tensor copies, tile_rows (2 or 4) rows
+// per CTA, the map's box (bit 2 of *tflag when a copy never completed).
+// pdl: programmatic dependent launch on the column pass before it.
 template <typename R>
 cudaError_t launch_rows_inv(const void *oh, const RowOut &o, int nr, int nphi, const void *tw_row,
                             const void *twp_row, const R *rcen, unsigned int *flag, cudaStream_t s, int row0 = 0,
                             int nrows_run = -1, const CUtensorMap *tm = nullptr, unsigned int *tflag = nullptr,
-                            bool pdl = false);
+                            bool pdl = false, int tile_rows = 2);
 
 // Indirect term (App. E): out[2 a + {0, 1}] = (A_a, B_a) in FP64; partial
 // holds indirect_blocks(nphi) x 4 doubles.
@@ -155,6 +163,8 @@ struct sg_plan {
     cudaStream_t cstream = nullptr;       // sg_solve_host: copy stream of the pipelined solve
     cudaEvent_t cev[2 * 16] = {};         // sg_solve_host: per-chunk copy / compute events
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};   // sg_set_stage_events
+    int rows_fwd = 4, rows_inv = 2;       // launch tiles (sg_set_tiles): rows per CTA of the row transforms
+    int cols_staging = -1;                // column-pass staging (-1: default, 0 all at once, 1 per step)
     bool tm_rows = false;                 // tensor maps below are valid (rows_tma_eligible)
     CUtensorMap tm_sh{}, tm_oh{};         // the row transforms' views of sh and oh
     char err[256] = {0};

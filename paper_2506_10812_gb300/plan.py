@@ -190,6 +190,24 @@ class Plan:
             st = self._lib.sg_set_column_engine(self._h, N.ENGINES[engine])
         N.check(st, self._h, "sg_set_column_engine")
 
+    @property
+    def tiles(self):
+        """Launch tiles: {"rows_fwd": 2|4, "rows_inv": 2|4, "cols_staging": "all"|"step"}."""
+        t = N.SgTiles()
+        N.check(self._lib.sg_get_tiles(self._h, ctypes.byref(t)), self._h, "sg_get_tiles")
+        names = {v: k for k, v in N.COLS_STAGING.items()}
+        return {"rows_fwd": t.rows_fwd, "rows_inv": t.rows_inv, "cols_staging": names[t.cols_staging]}
+
+    def set_tiles(self, rows_fwd=None, rows_inv=None, cols_staging=None):
+        """Set any of the launch tiles (the others keep their values)."""
+        cur = self.tiles
+        t = N.SgTiles(rows_fwd if rows_fwd is not None else cur["rows_fwd"],
+                      rows_inv if rows_inv is not None else cur["rows_inv"],
+                      N.COLS_STAGING[cols_staging if cols_staging is not None else cur["cols_staging"]])
+        with torch.cuda.device(self.device):
+            st = self._lib.sg_set_tiles(self._h, ctypes.byref(t))
+        N.check(st, self._h, "sg_set_tiles")
+
     def sync(self):
         with torch.cuda.device(self.device):
             st = self._lib.sg_sync(self._h, self._stream())
