@@ -197,7 +197,7 @@ __device__ __forceinline__ void cols_pair_steps(const cplx<R> *__restrict__ sh, 
         for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(sh + (size_t)a * N * nr + blk(m, t + T * e, nr), pf);
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
-        fft_any<true, LC>(v, L, T, t, xb, tw, eng.template d16<true>());
+        fft_any<true, LC, true>(v, L, T, t, xb, tw, eng.template d16<true>());
         // every thread's loads of this column were consumed before the
         // transform's first barrier: the column is dead
         if (discard) l2_discard_range(sh + (size_t)a * N * nr + blk(m, 0, nr), (size_t)nr * sizeof(C), t, T);
@@ -300,7 +300,7 @@ k_cols(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<R> 
         for (int e = 0; e < 8; ++e) v[e] = ld_cg_hint(sh + (size_t)a * N * nr + blk(m, t + T * e, nr), pf);
 #pragma unroll
         for (int e = 8; e < 16; ++e) v[e] = mkc<C>(0, 0);   // radial zero padding
-        fft_any<true, LC>(v, L, T, t, xb, tw);
+        fft_any<true, LC, true>(v, L, T, t, xb, tw);
         // every thread's loads of this column were consumed before the
         // transform's first barrier: the column is dead
         if (discard) l2_discard_range(sh + (size_t)a * N * nr + blk(m, 0, nr), (size_t)nr * sizeof(C), t, T);

@@ -184,12 +184,9 @@ template <bool FWD, int OFF, int S, typename T> __device__ __forceinline__ void 
     }
 }
 
-// In-place 16-point DFT on a[0..15] (natural order in and out).
-template <bool FWD, typename T> __device__ __forceinline__ void dft16(T (&a)[16])
+// Second half of the 16-point DFT below (after its first radix-4 stage).
+template <bool FWD, typename T> __device__ __forceinline__ void dft16_tail(T (&a)[16])
 {
-    // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^{n2 k1}, DFT4 over n2
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) dft4<FWD>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
     // a[4 k1 + n2] = B[n2][k1]
     a[5] = w16<FWD, 1>(a[5]);
     a[6] = w16<FWD, 2>(a[6]);
@@ -210,6 +207,51 @@ template <bool FWD, typename T> __device__ __forceinline__ void dft16(T (&a)[16]
     for (int k1 = 0; k1 < 4; ++k1)
 #pragma unroll
         for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = b[4 * k1 + k2];
+}
+
+// In-place 16-point DFT on a[0..15] (natural order in and out).
+template <bool FWD, typename T> __device__ __forceinline__ void dft16(T (&a)[16])
+{
+    // n = 4 n1 + n2, k = k1 + 4 k2: DFT4 over n1, twiddle W16^{n2 k1}, DFT4 over n2
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<FWD>(a[n2], a[4 + n2], a[8 + n2], a[12 + n2]);
+    dft16_tail<FWD>(a);
+}
+
+// The same DFT when a[8..15] are zero (the radially zero-padded half of a
+// forward column transform): each first-stage radix 4 has two inputs,
+// X = x0 + x1, x0 -+ i x1, x0 - x1, x0 +- i x1 (4 packed instructions
+// instead of 9).  Zero operands cannot be folded by the compiler (x + 0 is not
+// x for x = -0), so the pruning is explicit.
+template <bool FWD> __device__ __forceinline__ void dft16_half(float2 (&a)[16])
+{
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        const float2 x0 = a[n2], x1 = a[4 + n2];
+        const float2 u = make_float2(x1.y, x1.x);
+        a[n2] = padd(x0, x1);
+        a[8 + n2] = psub(x0, x1);
+        if (FWD) {   // x0 - i x1 = x0 + (u.x, -u.y),  x0 + i x1 = x0 + (-u.x, u.y)
+            a[4 + n2] = pfma_sign<1, -1>(u, x0);
+            a[12 + n2] = pfma_sign<-1, 1>(u, x0);
+        } else {
+            a[4 + n2] = pfma_sign<-1, 1>(u, x0);
+            a[12 + n2] = pfma_sign<1, -1>(u, x0);
+        }
+    }
+    dft16_tail<FWD>(a);
+}
+template <bool FWD, typename T> __device__ __forceinline__ void dft16_half(T (&a)[16])
+{
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        const T x0 = a[n2], x1 = a[4 + n2];
+        a[n2] = cadd(x0, x1);
+        a[8 + n2] = csub(x0, x1);
+        a[4 + n2] = cadd(x0, FWD ? cmul_mi(x1) : cmul_i(x1));
+        a[12 + n2] = cadd(x0, FWD ? cmul_i(x1) : cmul_mi(x1));
+    }
+    dft16_tail<FWD>(a);
 }
 
 // Padded shared-memory index: one extra slot every 16 elements makes the
@@ -350,6 +392,8 @@ __device__ __forceinline__ void load_pass_tw(const T *__restrict__ tp, int t, T 
 // in for it.
 template <bool FWD> struct RegDft16 {
     template <typename T> __device__ __forceinline__ void operator()(T (&v)[16]) const { dft16<FWD>(v); }
+    // first pass of a transform whose inputs v[8..15] are zero
+    template <typename T> __device__ __forceinline__ void half(T (&v)[16]) const { dft16_half<FWD>(v); }
 };
 
 template <bool FWD, int L, int Ns, typename T, typename D16 = RegDft16<FWD>>
@@ -416,11 +460,13 @@ __device__ __forceinline__ void fft_ct_pass(T (&v)[16], int t, T *xb, const T *_
     }
 }
 
-template <bool FWD, int L, typename T, typename D16 = RegDft16<FWD>>
+// HALF: the inputs v[8..15] (x[L/2 ..]) are zero and the first pass skips them.
+template <bool FWD, int L, bool HALF = false, typename T, typename D16 = RegDft16<FWD>>
 __device__ __forceinline__ void fft_ct(T (&v)[16], int t, T *xb, const T *__restrict__ twp, D16 &&d16 = D16{})
 {
     static_assert(L >= 256 && (L & (L - 1)) == 0, "compile-time FFT needs a power of two >= 256");
-    d16(v);
+    if constexpr (HALF) d16.half(v);
+    else d16(v);
     T b[12];
     load_pass_tw<L, 16>(twp, t, b);
     exchange_ct<1, L / 16>(v, t, xb);
@@ -428,12 +474,13 @@ __device__ __forceinline__ void fft_ct(T (&v)[16], int t, T *xb, const T *__rest
 }
 
 // Compile-time length when LC > 0, runtime length L otherwise (the
-// butterfly policy d16 applies to the compile-time lengths).
-template <bool FWD, int LC, typename T, typename D16 = RegDft16<FWD>>
+// butterfly policy d16 and the zero-half pruning HALF apply to the
+// compile-time lengths).
+template <bool FWD, int LC, bool HALF = false, typename T, typename D16 = RegDft16<FWD>>
 __device__ __forceinline__ void fft_any(T (&v)[16], int L, int T_, int t, T *xb, const T *__restrict__ twp,
                                         D16 &&d16 = D16{})
 {
-    if constexpr (LC > 0) fft_ct<FWD, LC>(v, t, xb, twp, d16);
+    if constexpr (LC > 0) fft_ct<FWD, LC, HALF>(v, t, xb, twp, d16);
     else fft_reg<FWD>(v, L, T_, t, xb, twp);
 }
 

@@ -106,6 +106,8 @@ struct TcState {
 
 template <int L, int MODE, bool FWD> struct TcDft16 {
     TcState *st;
+    // a zero upper half saves nothing in a dense product
+    __device__ __forceinline__ void half(float2 (&v)[16]) const { (*this)(v); }
     __device__ __forceinline__ void operator()(float2 (&v)[16]) const
     {
         using M = TcMode<MODE>;
