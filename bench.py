@@ -660,9 +660,9 @@ def run_batch(args):
         p.close()
 
 
-def surrogate_flops(nr, nphi, B):
+def surrogate_flops(nr, nphi, B, M1=16, K1=32):
     """Multiply-add work (x2) of one surrogate forward pass."""
-    C, M1, K1, CIN, QH = 32, 16, 32, 7, 64
+    C, CIN, QH = 32, 7, 64
     n = B * nr * nphi
     per_layer = (2 * (2 * M1) * C * nphi * B * nr            # truncated phi-DFT
                  + 2 * (2 * K1) * (2 * M1 * C) * nr * B      # truncated radial DFT
@@ -675,20 +675,16 @@ def surrogate_flops(nr, nphi, B):
 
 def run_surrogate(args):
     """The spectral neural-operator surrogate on the 512 x 1024 gas + dust
-    workload: trained on seeded fields the exact path labels, validated on
-    held-out fields, timed against the exact FFT path; Surrogate.solve uses
-    it only below the 1e-3 relative-error gate."""
+    workload at two retained-mode sizes (16 azimuthal x 16 radial, and 16 x
+    32): each trained on seeded fields the exact path labels, validated on
+    held-out fields, its forward pass timed with the tcgen05 GEMMs and with
+    the mma.sync ones, beside the exact FFT path; Surrogate.solve uses it
+    only below the 1e-3 relative-error gate."""
     import torch
+    from paper_2506_10812_gb300 import _native as N
     from paper_2506_10812_gb300.surrogate import GATE, Surrogate
     dev = torch.device("cuda", torch.cuda.current_device())
-    S = Surrogate(nr=512, nphi=1024, batch=2, seed=0, device=dev)
-    t0 = time.perf_counter()
-    hist = S.train(args.sur_steps, lr=2e-3, seed0=1000)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    rel = S.validate(list(range(10 ** 6, 10 ** 6 + 32)))
-    # inference: network forward on a loaded pair of discs vs the exact solve of both
-    hs = S.load([10 ** 6 + 100, 10 ** 6 + 101])
+    lib = N.load()
     K, W = args.steps, args.warmup
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -705,36 +701,80 @@ def run_surrogate(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(e) for a, e in ev) / K
 
-    ms_net = timed(S.forward)
-    plans = [S._plan(h, St) for h, St in hs]
-    outs = [{"gr_g": S.gr[b], "gphi_g": S.gphi[b]} for b in range(2)]
-    ms_exact = timed(lambda: [p.solve(S.sg[b], S.sd[b], out=o) for b, (p, o) in enumerate(zip(plans, outs))])
-    cells = 2 * S.npix
-    peak = None
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak = float(json.load(f)["bf16_tflops"])
+            pk = json.load(f)
+        peak_tf, peak_bw = float(pk["bf16_tflops"]), float(pk["hbm_gbs"])
     except (OSError, KeyError, ValueError):
-        peak = 1900.0
-    fl = surrogate_flops(S.nr, S.nphi, 2)
-    achieved = fl / (ms_net * 1e-3) / 1e12
+        peak_tf, peak_bw = 1900.0, 6800.0
+    variants, exact, clk = {}, None, None
+    for name, mp, mr in (("16x16", 16, 16), ("16x32", 16, 32)):
+        S = Surrogate(nr=512, nphi=1024, batch=2, seed=0, device=dev, modes_phi=mp, modes_r=mr)
+        t0 = time.perf_counter()
+        hist = S.train(args.sur_steps, lr=2e-3, seed0=1000)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        rel = S.validate(list(range(10 ** 6, 10 ** 6 + 32)))
+        N.check(lib.sg_nn_check(None), what="sg_nn_check")
+        hs = S.load([10 ** 6 + 100, 10 ** 6 + 101])
+        S.k.count = {}
+        S.forward()
+        count, S.k.count = S.k.count, None
+        ms = {}
+        for eng, code in (("tcgen05", N.SG_NN_GEMM_TCGEN05), ("mma_sync", N.SG_NN_GEMM_MMA_SYNC)):
+            N.check(lib.sg_nn_set_gemm_engine(code), what="sg_nn_set_gemm_engine")
+            if eng == "tcgen05" and clk is None:
+                sampler = ClockSampler(dev.index)
+                sampler.start()
+                time.sleep(0.1)
+                t_b = time.time()
+                ms[eng] = timed(S.forward)
+                clk = sampler.stop(t_b, time.time())
+            else:
+                ms[eng] = timed(S.forward)
+        N.check(lib.sg_nn_set_gemm_engine(N.SG_NN_GEMM_TCGEN05), what="sg_nn_set_gemm_engine")
+        N.check(lib.sg_nn_check(None), what="sg_nn_check")
+        if exact is None:
+            plans = [S._plan(h, St) for h, St in hs]
+            outs = [{"gr_g": S.gr[b], "gphi_g": S.gphi[b]} for b in range(2)]
+            ms_exact = timed(lambda: [p.solve(S.sg[b], S.sd[b], out=o)
+                                      for b, (p, o) in enumerate(zip(plans, outs))])
+            exact = {"ms": ms_exact, "cells_per_s": 2 * S.npix / (ms_exact * 1e-3)}
+        fl = surrogate_flops(S.nr, S.nphi, 2, mp, mr)
+        t = ms["tcgen05"] * 1e-3
+        variants[name] = {
+            "modes": {"azimuthal": mp, "radial": mr},
+            "training": {"steps": args.sur_steps, "fields": 2 * args.sur_steps, "seconds": train_s,
+                         "final_loss": hist[-1] if hist else None},
+            "validation_rel_l2": {"gr_g": float(rel[0]), "gphi_g": float(rel[1]), "fields": 32},
+            "gate": GATE, "surrogate_used": bool(S.val_error <= GATE),
+            "forward_ms": {"tcgen05_gemm": ms["tcgen05"], "mma_sync_gemm": ms["mma_sync"]},
+            "cells_per_s": 2 * S.npix / t,
+            "launches_per_forward": count.get("launches", 0), "gemms_per_forward": count.get("gemms", 0),
+            "roofline": {"bound": "hbm", "kernel": "surrogate forward (all launches)",
+                         "achieved": round(count.get("gemm_bytes", 0) / t / 1e9, 1), "peak": peak_bw,
+                         "unit": "GB/s", "frac": round(count.get("gemm_bytes", 0) / t / 1e9 / peak_bw, 4),
+                         "traffic": None,
+                         "algorithmic_bytes_per_forward": count.get("gemm_bytes", 0),
+                         "bytes_note": "each GEMM operand read or written once; elementwise kernels not counted"},
+            "tensor": {"achieved_tflops": round(fl / t / 1e12, 2), "peak": peak_tf,
+                       "frac": round(fl / t / 1e12 / peak_tf, 5), "algorithmic_flops_per_forward": fl},
+        }
+        del S
+        torch.cuda.empty_cache()
+    head = variants["16x16"]
     result = {"metric": "surrogate cells/s and relative L2 vs the exact path (gate 1e-3)",
-              "value": cells / (ms_net * 1e-3), "unit": "cells/s", "n_gpus": 1, "steps": K, "warmup": W,
-              "ms_per_step": ms_net, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-              "dtype": "bf16 (FP32 accumulate)", "data": "synthetic (seeded log-normal + spiral + clump fields)",
+              "value": head["cells_per_s"], "unit": "cells/s", "n_gpus": 1, "steps": K, "warmup": W,
+              "ms_per_step": head["forward_ms"]["tcgen05_gemm"], "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "bf16 (FP32 accumulate)",
+              "data": "synthetic (seeded log-normal + spiral + clump fields)",
               "config": {"workload": "2 gas + dust discs 512x1024, r in [0.1, 5], h_g in {0.03..0.1}, "
                                      "St in {0.01, 0.1, 1}; 4-layer width-32 spectral neural operator, "
-                                     "16 x 32 modes", "l2": "flushed between timed steps (256 MiB write)"},
-              "training": {"steps": args.sur_steps, "fields": 2 * args.sur_steps, "seconds": train_s,
-                           "final_loss": hist[-1] if hist else None},
-              "validation_rel_l2": {"gr_g": float(rel[0]), "gphi_g": float(rel[1]), "fields": 32},
-              "gate": GATE, "surrogate_used": bool(S.val_error <= GATE),
-              "exact_path": {"ms": ms_exact, "cells_per_s": cells / (ms_exact * 1e-3)},
-              "roofline": {"bound": "tensor", "kernel": "surrogate forward (BF16 GEMMs + mixing)",
-                           "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
-                           "frac": round(achieved / peak, 5), "traffic": None,
-                           "algorithmic_flops_per_launch": fl},
-              "gpu_launches": K * 40}
+                                     "16 x 16 retained modes (headline) and 16 x 32",
+                         "l2": "flushed between timed steps (256 MiB write)"},
+              "variants": variants, "exact_path": exact,
+              "roofline": head["roofline"], "clocks": clk,
+              "gpu_launches": K * head["launches_per_forward"]}
     print(json.dumps(result), flush=True)
 
 

@@ -415,13 +415,25 @@ sg_status sg_set_column_engine(sg_plan *plan, int32_t engine);
  * non-positive sizes, SG_ERR_CUDA for a launch error.
  * ---------------------------------------------------------------------- */
 
-/* Batched GEMM on the tensor cores (mma.sync m16n8k16, bf16 in, FP32
- * accumulate): for z < batch,
+/* Batched GEMM on the tensor cores (bf16 in, FP32 accumulate): for
+ * z < batch,
  *   C[z] = alpha op(A[z]) B[z] + beta C[z] (+ bias[n]),
  * op(A) = A ([M][K], leading dim lda) or, with trans_a, A^T (A stored [K][M]);
  * B [K][N] (ldb); C [M][N] (ldc) float and/or C_bf16 (same layout, bf16);
  * stride_* are batch strides in elements (0 broadcasts); bias float [N] or
- * NULL; beta != 0 needs C.  batch <= 65535.                               */
+ * NULL; beta != 0 needs C.  batch <= 65535, N <= 65535 x 128.
+ * Engine (sg_nn_set_gemm_engine, process-wide): SG_NN_GEMM_TCGEN05 (default)
+ * runs 128 x {32, 64, 128} tiles of tcgen05.mma with the accumulator in
+ * tensor memory; SG_NN_GEMM_MMA_SYNC the warp-level m16n8k16 kernel, kept
+ * for comparison.  Both sum K in the same 16-element groups but in a
+ * different order, so they agree to FP32 rounding.  A tensor-core wait that
+ * gives up (bounded; never expected) leaves that tile unwritten and is
+ * reported by sg_nn_check.                                                */
+enum { SG_NN_GEMM_TCGEN05 = 0, SG_NN_GEMM_MMA_SYNC = 1 };
+sg_status sg_nn_set_gemm_engine(int32_t engine);
+/* Synchronise `stream`; SG_ERR_TIMEOUT if a tensor-core wait of an
+ * sg_nn_gemm on this device gave up since the last check (clears it).   */
+sg_status sg_nn_check(void *stream);
 sg_status sg_nn_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, float alpha, const void *A, int32_t lda,
                      int64_t stride_a, int32_t trans_a, const void *B, int32_t ldb, int64_t stride_b, float beta,
                      float *C, int32_t ldc, int64_t stride_c, void *C_bf16, const float *bias, void *stream);

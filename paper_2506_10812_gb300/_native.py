@@ -20,6 +20,8 @@ SG_COMP_PHI, SG_COMP_R, SG_COMP_AZ = 0, 1, 2
 SG_CHECK_FINITE = 2
 SG_BATCH_HOST_GATE = 4
 SG_BATCH_ORDER_PIPELINED, SG_BATCH_ORDER_STAGED = 0, 1
+SG_NN_GEMM_TCGEN05, SG_NN_GEMM_MMA_SYNC = 0, 1
+SG_COLS_STAGE_ALL, SG_COLS_STAGE_STEP = 0, 1
 SG_ENGINE_FFT32, SG_ENGINE_DFT_FP16X3, SG_ENGINE_DFT_BF16X3, SG_ENGINE_DFT_FP16, SG_ENGINE_DFT_BF16, \
     SG_ENGINE_TC_BF16X3, SG_ENGINE_TC_TF32X3, SG_ENGINE_TC_BF16 = range(8)
 ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf16": 4,
@@ -29,7 +31,7 @@ ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf1
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
            "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_set_column_engine", "sg_get_tiles", "sg_set_tiles", "sg_batch_create", "sg_batch_solve",
            "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_tune_results", "sg_batch_tile_trials", "sg_batch_destroy",
-           "sg_batch_last_error", "sg_nn_gemm", "sg_nn_spec_combine", "sg_nn_spec_combine_bwd", "sg_nn_modemix",
+           "sg_batch_last_error", "sg_nn_set_gemm_engine", "sg_nn_check", "sg_nn_gemm", "sg_nn_spec_combine", "sg_nn_spec_combine_bwd", "sg_nn_modemix",
            "sg_nn_modemix_bwd", "sg_nn_act", "sg_nn_act_bwd", "sg_nn_colsum", "sg_nn_rel_l2", "sg_nn_adam", "sg_nn_cast",
            "sg_nn_transpose", "sg_nn_fields", "sg_nn_pack_inputs", "sg_nn_pack_targets", "sg_destroy", "sg_status_string", "sg_last_error")
 
@@ -146,6 +148,10 @@ def load() -> ctypes.CDLL:
         "sg_nn_pack_inputs": [i32, i32, i32, vp, vp, vp, vp, vp],
         "sg_nn_pack_targets": [i32, i64, vp, vp, vp, vp, i32, vp],
     }
+    lib.sg_nn_set_gemm_engine.argtypes = [i32]
+    lib.sg_nn_set_gemm_engine.restype = st
+    lib.sg_nn_check.argtypes = [vp]
+    lib.sg_nn_check.restype = st
     for name, args in nn.items():
         getattr(lib, name).argtypes = args
         getattr(lib, name).restype = st

@@ -283,6 +283,16 @@ __device__ __forceinline__ void umma_tmem_a(uint32_t d_tmem, uint32_t a_tmem, ui
                      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
                      : "memory");
 }
+// D[tmem] (+)= A[smem] B[smem] (kind::f16, both operands K-major through
+// shared-memory descriptors); issued by one thread.
+__device__ __forceinline__ void umma_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+                 "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
 // One arrive on the mbarrier once every product this thread issued before
 // it has completed.
 __device__ __forceinline__ void umma_commit(uint64_t *bar)
@@ -312,6 +322,21 @@ __device__ __forceinline__ void tmem_ld16c(uint32_t taddr, float2 (&v)[16])
                    "=f"(v[9].x), "=f"(v[9].y), "=f"(v[10].x), "=f"(v[10].y), "=f"(v[11].x), "=f"(v[11].y),
                    "=f"(v[12].x), "=f"(v[12].y), "=f"(v[13].x), "=f"(v[13].y), "=f"(v[14].x), "=f"(v[14].y),
                    "=f"(v[15].x), "=f"(v[15].y)
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// 32 FP32 cells of this thread's lane, columns col .. col + 31, waited for.
+__device__ __forceinline__ void tmem_ld32f(uint32_t taddr, float (&v)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                 "[%32];\n\ttcgen05.wait::ld.sync.aligned;"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]),
+                   "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]),
+                   "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]),
+                   "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]),
+                   "=f"(v[29]), "=f"(v[30]), "=f"(v[31])
                  : "r"(taddr)
                  : "memory");
 }

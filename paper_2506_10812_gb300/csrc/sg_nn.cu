@@ -8,7 +8,11 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <type_traits>
+
 #include "sg.h"
+#include "sg_mem.cuh"
 
 namespace {
 
@@ -167,7 +171,337 @@ k_gemm(int M, int N, int K, float alpha, const __nv_bfloat16 *__restrict__ A, in
             }
 }
 
+// ----------------------------------------------------------------------
+// The same GEMM on the tcgen05 tensor cores.  One CTA of 128 threads owns a
+// 128 x BN tile of C (BN = 32, 64 or 128) and walks K in steps of 64: every
+// thread loads part of the A and B tiles into registers, stores them into
+// shared memory in the K-major core-matrix layout the tensor core reads
+// (transposing B, and A^T, 8 x 8 blocks in registers), and one thread issues
+// four 128 x BN x 16 BF16 products accumulating in FP32 in tensor memory and
+// commits them to the stage's mbarrier.  Two shared-memory stages: the loads
+// of step s + 1 run while the products of step s do.  The epilogue reads
+// each thread's row of the accumulator (warp w: rows 32 w .. 32 w + 31)
+// and applies alpha, bias and beta.
+//
+// Tile layout: row r, K chunk c (8 elements, 16 bytes) at
+//   (r / 8) SBO + c LBO + (r % 8) 16 bytes,  LBO = 144, SBO = 8 LBO + 16,
+// i.e. core matrices of 8 rows x 16 bytes, padded so that the row-per-lane
+// stores of A and the block-per-thread stores of B are free of bank
+// conflicts.
+constexpr int TC_BM = 128, TC_BK = 64, TC_LBO = 144, TC_SBO = 8 * TC_LBO + 16;
+
+__device__ unsigned g_nn_flag;   // bit 0: a tensor-core wait gave up
+
+__host__ __device__ constexpr unsigned tc_tile_bytes(int rows) { return (unsigned)(rows / 8) * TC_SBO; }
+__host__ __device__ constexpr unsigned tc_stage_bytes(int bn) { return tc_tile_bytes(TC_BM) + tc_tile_bytes(bn); }
+// NST stages, or the epilogue's FP32 tile (row stride bn + 4) if larger;
+// then two mbarriers and the tensor-memory address
+__host__ __device__ constexpr unsigned tc_data_bytes(int bn, int nst)
+{
+    return nst * tc_stage_bytes(bn) > (unsigned)TC_BM * (bn + 4) * 4 ? nst * tc_stage_bytes(bn)
+                                                                     : (unsigned)TC_BM * (bn + 4) * 4;
+}
+__host__ __device__ constexpr unsigned tc_smem_bytes(int bn, int nst) { return tc_data_bytes(bn, nst) + 32; }
+// resident CTAs per SM the launch bounds aim at (shared memory allows them;
+// tensor memory: at most 512 columns in all)
+__host__ __device__ constexpr int tc_min_blocks(int bn, int nst)
+{
+    return nst == 1 ? (bn == 32 ? 6 : bn == 64 ? 5 : 3) : (bn == 128 ? 3 : 4);
+}
+__device__ __forceinline__ unsigned tc_off(int r, int c) { return (r >> 3) * TC_SBO + c * TC_LBO + (r & 7) * 16; }
+
+__device__ __forceinline__ uint32_t word_of(const uint4 &u, int w)
+{
+    return w == 0 ? u.x : w == 1 ? u.y : w == 2 ? u.z : u.w;
+}
+__device__ __forceinline__ void set_word(uint4 &u, int w, uint32_t v)
+{
+    if (w == 0) u.x = v;
+    else if (w == 1) u.y = v;
+    else if (w == 2) u.z = v;
+    else u.w = v;
+}
+// 8 x 8 transpose of 16-bit elements: r[i] holds elements 0..7 of row i,
+// o[j] receives element j of rows 0..7 (lower address first).
+__device__ __forceinline__ void transpose8x8(const uint4 (&r)[8], uint4 (&o)[8])
+{
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t a = word_of(r[2 * p], w), b = word_of(r[2 * p + 1], w);
+            set_word(o[2 * w], p, __byte_perm(a, b, 0x5410));
+            set_word(o[2 * w + 1], p, __byte_perm(a, b, 0x7632));
+        }
+}
+
+// 8 consecutive bf16 of a row at (row, col) of a row-major matrix with
+// leading dimension ld, zero outside rows < nrow, cols < ncol; vec: 16-byte
+// loads allowed where the 8 are in range.
+__device__ __forceinline__ uint4 ld8(const __nv_bfloat16 *__restrict__ X, int ld, int row, int col, int nrow,
+                                     int ncol, int vec)
+{
+    uint4 u = make_uint4(0, 0, 0, 0);
+    if (row >= nrow || col >= ncol) return u;
+    const __nv_bfloat16 *p = X + (size_t)row * ld + col;
+    if (vec && col + 8 <= ncol) return __ldg(reinterpret_cast<const uint4 *>(p));
+    unsigned short e[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) e[j] = col + j < ncol ? __bfloat16_as_ushort(p[j]) : (unsigned short)0;
+    u.x = e[0] | ((uint32_t)e[1] << 16);
+    u.y = e[2] | ((uint32_t)e[3] << 16);
+    u.z = e[4] | ((uint32_t)e[5] << 16);
+    u.w = e[6] | ((uint32_t)e[7] << 16);
+    return u;
+}
+
+template <bool TA, int BN, int NST, bool FOLD = false>
+__global__ void __launch_bounds__(128, tc_min_blocks(BN, NST))
+k_gemm_tc(int M, int N, int K, float alpha, const __nv_bfloat16 *__restrict__ A, int lda, long long sa,
+          const __nv_bfloat16 *__restrict__ B, int ldb, long long sb, float beta, float *__restrict__ C, int ldc,
+          long long sc, __nv_bfloat16 *__restrict__ Cb, const float *__restrict__ bias, int vecA, int vecB,
+          int batch, int fold)
+{
+    using namespace sg;
+    extern __shared__ __align__(128) unsigned char sm[];
+    constexpr unsigned AB = tc_tile_bytes(TC_BM), ST = tc_stage_bytes(BN);
+    constexpr uint32_t IDESC = umma_idesc(TC_BM, BN, 1);
+    static_assert(NST == 1 || NST == 2, "one or two shared-memory stages");
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + tc_data_bytes(BN, NST));
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + tc_data_bytes(BN, NST) + 16);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // fold > 1 (A shared by the batch, N % 8 == 0): the tile's columns are
+    // `fold` consecutive batch entries side by side, column nn = (nn / N)-th
+    // entry, its column nn % N; otherwise one batch entry per CTA.
+    static_assert(!FOLD || BN == 128, "folded tiles are 128 columns wide");
+    const int m0 = blockIdx.x * TC_BM;
+    const int z0 = FOLD ? blockIdx.z * fold : blockIdx.z, n0 = FOLD ? 0 : blockIdx.y * BN;
+    A += z0 * sa;
+    if (warp == 0) {
+        tmem_alloc(tslot, BN);
+        tmem_relinquish();
+    }
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem = *tslot;
+    const unsigned sbase = smem_u32(sm);
+
+    // Per-thread share of a stage.  A ([M][K]): the thread's row 32 warp +
+    // lane, its 8 chunks of 8 k.  A^T ([K][M]) and B ([K][N]): one 8 k x 8
+    // m (or n) block, transposed; thread (blk, kc) = (t / 8, t % 8).
+    constexpr int NBB = BN;                 // B blocks per stage: BN / 8 n-blocks x 8 k-chunks
+    uint4 ra[8], rb[8];
+    const int kc = t & 7, blk = t >> 3;
+    auto load = [&](int s) {
+        const int k0 = s * TC_BK;
+        if constexpr (!TA) {
+            const int r = m0 + 32 * warp + lane;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) ra[c] = ld8(A, lda, r, k0 + 8 * c, M, K, vecA);
+        } else {
+            // A^T block: rows k0 + 8 kc .. + 7 of the stored [K][M], columns m0 + 8 blk .. + 7
+#pragma unroll
+            for (int i = 0; i < 8; ++i) ra[i] = ld8(A, lda, k0 + 8 * kc + i, m0 + 8 * blk, K, M, vecA);
+        }
+        if (t < NBB) {
+            int zb = z0, col = n0 + 8 * blk;
+            if constexpr (FOLD) {
+                zb = z0 + (8 * blk) / N;
+                col = (8 * blk) % N;
+            }
+            const bool live = !FOLD || (8 * blk < fold * N && zb < batch);
+            const __nv_bfloat16 *Bz = B + zb * sb;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                rb[i] = live ? ld8(Bz, ldb, k0 + 8 * kc + i, col, K, N, vecB) : make_uint4(0, 0, 0, 0);
+        }
+    };
+    auto store = [&](int b) {
+        unsigned char *sa_ = sm + b * ST, *sb_ = sa_ + AB;
+        if constexpr (!TA) {
+            const int r = 32 * warp + lane;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4 *>(sa_ + tc_off(r, c)) = ra[c];
+        } else {
+            uint4 o[8];
+            transpose8x8(ra, o);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(sa_ + tc_off(8 * blk + j, kc)) = o[j];
+        }
+        if (t < NBB) {
+            uint4 o[8];
+            transpose8x8(rb, o);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4 *>(sb_ + tc_off(8 * blk + j, kc)) = o[j];
+        }
+    };
+
+    const int S = (K + TC_BK - 1) / TC_BK;
+    bool ok = true;
+    load(0);
+    for (int s = 0; s < S; ++s) {
+        const int b = s % NST;
+        // the products of step s - NST read this buffer
+        if (s >= NST) ok = mbar_wait_bounded(&bar[b], (unsigned)(((s - NST) / NST) & 1), &g_nn_flag, 1u);
+        if (__syncthreads_or(!ok)) break;
+        store(b);
+        fence_proxy_async();               // generic-proxy stores, visible to the tensor core
+        __syncthreads();
+        if (t == 0) {
+            tmem_fence_after();
+            const unsigned a0 = sbase + b * ST, b0 = a0 + AB;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                umma_ss(tmem, umma_sdesc(a0 + 2 * kk * TC_LBO, TC_LBO, TC_SBO),
+                        umma_sdesc(b0 + 2 * kk * TC_LBO, TC_LBO, TC_SBO), IDESC, (s > 0 || kk > 0) ? 1u : 0u);
+            umma_commit(&bar[b]);
+        }
+        if (s + 1 < S) load(s + 1);
+    }
+    // every product of the tile (the last commit covers all earlier ones)
+    if (ok) ok = mbar_wait_bounded(&bar[(S - 1) % NST], (unsigned)(((S - 1) / NST) & 1), &g_nn_flag, 1u);
+    if (!ok && NST == 2 && S >= 2)   // let the other stage's products finish before the memory is released
+        mbar_wait_bounded(&bar[(S - 2) % NST], (unsigned)(((S - 2) / NST) & 1), &g_nn_flag, 1u);
+    ok = !__syncthreads_or(!ok);
+    tmem_fence_after();
+    if (ok) {
+        // The products are complete, so the stage buffers are free: each
+        // warp moves its 32 accumulator rows there (row stride BN + 4 floats,
+        // conflict-free), then the CTA writes the tile out row by row with
+        // consecutive threads on consecutive columns.
+        constexpr int PS = BN + 4, CPR = BN / 4;
+        float *stg = reinterpret_cast<float *>(sm);
+        const int r = 32 * warp + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            tmem_ld32f(tmem + ((uint32_t)(32 * warp) << 16) + c0, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<float4 *>(stg + r * PS + c0 + 4 * j) =
+                    make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+        __syncthreads();
+        const bool vc = (ldc & 3) == 0 && (!C || ((uintptr_t)C & 15) == 0) && (!Cb || ((uintptr_t)Cb & 7) == 0) &&
+                        (sc & 3) == 0;
+        // output column nn of the tile -> (batch entry, column)
+        auto where = [&](int nn, int &zz, int &n) {
+            if constexpr (FOLD) {
+                zz = nn < fold * N ? z0 + nn / N : batch;
+                n = nn % N;
+            } else {
+                zz = z0;
+                n = n0 + nn;
+            }
+        };
+        // groups of G float4 per thread: the old C values of a group are
+        // loaded first, so that their loads are in flight together
+        constexpr int G = BN == 32 ? 4 : 8;
+#pragma unroll 1
+        for (int g0 = 0; g0 < CPR; g0 += G) {
+            float4 old[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                const int i = t + 128 * (g0 + u), rr = i / CPR, c4 = i - rr * CPR;
+                int zz, n;
+                where(4 * c4, zz, n);
+                const int m = m0 + rr;
+                old[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (C && beta != 0.f && vc && g0 + u < CPR && m < M && n + 4 <= N && zz < batch)
+                    old[u] = *reinterpret_cast<const float4 *>(C + zz * sc + (size_t)m * ldc + n);
+            }
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+                if (g0 + u >= CPR) break;
+                const int i = t + 128 * (g0 + u), rr = i / CPR, c4 = i - rr * CPR;
+                int zz, n;
+                where(4 * c4, zz, n);
+                const int m = m0 + rr;
+                if (m >= M || n >= N || zz >= batch) continue;
+                float *Cz = C ? C + zz * sc : nullptr;
+                __nv_bfloat16 *Cbz = Cb ? Cb + zz * sc : nullptr;
+                const float4 a = *reinterpret_cast<const float4 *>(stg + rr * PS + 4 * c4);
+                float x[4] = {alpha * a.x, alpha * a.y, alpha * a.z, alpha * a.w};
+                if (vc && n + 4 <= N) {
+                    if (bias) {
+                        if (((uintptr_t)bias & 15) == 0) {   // n is a multiple of 4
+                            const float4 bv = __ldg(reinterpret_cast<const float4 *>(bias + n));
+                            x[0] += bv.x;
+                            x[1] += bv.y;
+                            x[2] += bv.z;
+                            x[3] += bv.w;
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) x[j] += __ldg(bias + n + j);
+                        }
+                    }
+                    if (Cz) {
+                        if (beta != 0.f) {
+                            x[0] += beta * old[u].x;
+                            x[1] += beta * old[u].y;
+                            x[2] += beta * old[u].z;
+                            x[3] += beta * old[u].w;
+                        }
+                        *reinterpret_cast<float4 *>(Cz + (size_t)m * ldc + n) = make_float4(x[0], x[1], x[2], x[3]);
+                    }
+                    if (Cbz) {
+                        __nv_bfloat162 lo = __floats2bfloat162_rn(x[0], x[1]), hi = __floats2bfloat162_rn(x[2], x[3]);
+                        uint2 w;
+                        w.x = *reinterpret_cast<uint32_t *>(&lo);
+                        w.y = *reinterpret_cast<uint32_t *>(&hi);
+                        *reinterpret_cast<uint2 *>(Cbz + (size_t)m * ldc + n) = w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (n + j >= N) break;
+                        float y = x[j];
+                        if (bias) y += __ldg(bias + n + j);
+                        if (Cz) {
+                            float *p = Cz + (size_t)m * ldc + n + j;
+                            if (beta != 0.f) y += beta * *p;
+                            *p = y;
+                        }
+                        if (Cbz) Cbz[(size_t)m * ldc + n + j] = __float2bfloat16(y);
+                    }
+                }
+            }
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tmem_fence_after();
+        tmem_dealloc(tmem, BN);
+    }
+}
+
+int g_gemm_engine = SG_NN_GEMM_TCGEN05;
+
 }  // namespace
+
+extern "C" sg_status sg_nn_set_gemm_engine(int32_t engine)
+{
+    if (engine != SG_NN_GEMM_TCGEN05 && engine != SG_NN_GEMM_MMA_SYNC) return SG_ERR_ARG;
+    g_gemm_engine = engine;
+    return SG_OK;
+}
+
+extern "C" sg_status sg_nn_check(void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    unsigned f = 0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&f, g_nn_flag, sizeof(f));
+    const unsigned zero = 0;
+    if (e == cudaSuccess && f) e = cudaMemcpyToSymbol(g_nn_flag, &zero, sizeof(zero));
+    if (e != cudaSuccess) return SG_ERR_CUDA;
+    return f ? SG_ERR_TIMEOUT : SG_OK;
+}
 
 extern "C" sg_status sg_nn_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, float alpha, const void *A,
                                 int32_t lda, int64_t stride_a, int32_t trans_a, const void *B, int32_t ldb,
@@ -184,12 +518,62 @@ extern "C" sg_status sg_nn_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, 
     // 16-byte loads need 16-byte aligned rows in every batch entry
     const int vecA = (lda % 8 == 0) && (stride_a % 8 == 0) && ((uintptr_t)A % 16 == 0);
     const int vecB = (ldb % 8 == 0) && (stride_b % 8 == 0) && ((uintptr_t)B % 16 == 0);
-    if (trans_a)
+    if (g_gemm_engine == SG_NN_GEMM_TCGEN05) {
+        // the kernels' shared-memory limit, once per device
+        static std::atomic<unsigned long long> done{0};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SG_ERR_CUDA;
+        if (!((done.load() >> dev) & 1ull)) {
+            const void *fns[] = {
+                (const void *)k_gemm_tc<false, 32, 1>,  (const void *)k_gemm_tc<false, 64, 1>,
+                (const void *)k_gemm_tc<false, 128, 1>, (const void *)k_gemm_tc<true, 32, 1>,
+                (const void *)k_gemm_tc<true, 64, 1>,   (const void *)k_gemm_tc<true, 128, 1>,
+                (const void *)k_gemm_tc<false, 32, 2>,  (const void *)k_gemm_tc<false, 64, 2>,
+                (const void *)k_gemm_tc<false, 128, 2>, (const void *)k_gemm_tc<true, 32, 2>,
+                (const void *)k_gemm_tc<true, 64, 2>,   (const void *)k_gemm_tc<true, 128, 2>,
+                (const void *)k_gemm_tc<false, 128, 2, true>};
+            for (const void *f : fns)
+                if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(128, 2)) !=
+                    cudaSuccess)
+                    return SG_ERR_CUDA;
+            done.fetch_or(1ull << dev);
+        }
+        // A shared by a batch of narrow products with K > 64 (the azimuthal
+        // DFTs): fold batch entries side by side into 128-column tiles, so a
+        // CTA reads each A step once for all of them
+        const int fold =
+            (!trans_a && stride_a == 0 && K > TC_BK && N % 8 == 0 && N <= 64 && batch > 1) ? TC_BM / N : 1;
+        const int bn = fold > 1 ? 128 : N <= 32 ? 32 : N <= 64 ? 64 : 128, nst = K <= TC_BK ? 1 : 2;
+        const dim3 gt((M + TC_BM - 1) / TC_BM, fold > 1 ? 1 : (N + bn - 1) / bn, (batch + fold - 1) / fold);
+        if (gt.y > 65535) return SG_ERR_UNSUPPORTED;
+        auto go = [&](auto kern) {
+            kern<<<gt, 128, tc_smem_bytes(bn, nst), s>>>(M, N, K, alpha, a, lda, stride_a, b, ldb, stride_b, beta, C,
+                                                         ldc, stride_c, (__nv_bfloat16 *)C_bf16, bias, vecA, vecB,
+                                                         batch, fold);
+        };
+        auto pick = [&](auto ta) {
+            constexpr bool TA = decltype(ta)::value;
+            if (fold > 1 && !TA) {
+                go(k_gemm_tc<false, 128, 2, true>);
+            } else if (nst == 1) {
+                if (bn == 32) go(k_gemm_tc<TA, 32, 1>);
+                else if (bn == 64) go(k_gemm_tc<TA, 64, 1>);
+                else go(k_gemm_tc<TA, 128, 1>);
+            } else {
+                if (bn == 32) go(k_gemm_tc<TA, 32, 2>);
+                else if (bn == 64) go(k_gemm_tc<TA, 64, 2>);
+                else go(k_gemm_tc<TA, 128, 2>);
+            }
+        };
+        if (trans_a) pick(std::true_type{});
+        else pick(std::false_type{});
+    } else if (trans_a) {
         k_gemm<true><<<grid, 128, 0, s>>>(M, N, K, alpha, a, lda, stride_a, b, ldb, stride_b, beta, C, ldc, stride_c,
                                           (__nv_bfloat16 *)C_bf16, bias, vecA, vecB);
-    else
+    } else {
         k_gemm<false><<<grid, 128, 0, s>>>(M, N, K, alpha, a, lda, stride_a, b, ldb, stride_b, beta, C, ldc, stride_c,
                                            (__nv_bfloat16 *)C_bf16, bias, vecA, vecB);
+    }
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 

@@ -8,10 +8,10 @@ gas accelerations (g_r, g_phi):
     4 layers  v_{l+1} = act(S_l(v_l) + v_l W_l + b_l)   (act = GELU, none last)
     output    y = GELU(v4 Q1 + q1) Q2 + q2       (C -> 64 -> 2)
 
-where S_l is a spectral convolution that keeps 16 azimuthal modes m and 32
-radial modes k (16 non-negative, 16 negative): a truncated DFT along phi
-and r, a complex C x C channel mix per kept mode, and the inverse truncated
-DFT.  With truncated modes every transform is a product with a fixed DFT
+where S_l is a spectral convolution that keeps M1 azimuthal modes m and K1
+radial modes k (K1 / 2 non-negative, K1 / 2 negative; defaults 16 and 32,
+and 16 x 16 as the other studied size): a truncated DFT along phi and r, a
+complex C x C channel mix per kept mode, and the inverse truncated DFT.  With truncated modes every transform is a product with a fixed DFT
 matrix, so the forward and backward passes are batched BF16 tensor-core
 GEMMs (sg_nn_gemm, FP32 accumulation) plus the mode-mixing, activation and
 loss kernels of sg_nn.cu; weights are FP32 masters with BF16 copies and
@@ -33,8 +33,8 @@ from . import _native as N
 from .plan import Plan
 
 C = 32            # width
-M1 = 16           # azimuthal modes kept
-K1 = 32           # radial modes kept (16 + 16)
+M1 = 16           # azimuthal modes kept (default)
+K1 = 32           # radial modes kept (default; half non-negative, half negative)
 CIN = 7
 QH = 64           # projection hidden width
 NF = 32           # random Fourier features of the training fields
@@ -51,6 +51,7 @@ class _Lib:
     def __init__(self, device):
         self.lib = N.load()
         self.device = device
+        self.count = None      # when a dict: launches, GEMM flops and operand bytes are tallied into it
 
     def _s(self):
         return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
@@ -58,12 +59,23 @@ class _Lib:
     def call(self, name, *args):
         st = getattr(self.lib, name)(*args, self._s())
         N.check(st, None, name)
+        if self.count is not None:
+            self.count["launches"] = self.count.get("launches", 0) + 1
 
     def gemm(self, batch, M, Nn, K, A, lda, sa, B, ldb, sb, C=None, ldc=0, sc=0, Cb=None, alpha=1.0, beta=0.0,
              bias=None, trans_a=False, a_off=0):
         Ap = ctypes.c_void_p(A.data_ptr() + a_off * A.element_size())
         self.call("sg_nn_gemm", batch, M, Nn, K, alpha, Ap, lda, sa, 1 if trans_a else 0, _p(B), ldb, sb, beta,
                   _p(C), ldc, sc, _p(Cb), _p(bias))
+        if self.count is not None:
+            c = self.count
+            c["gemm_flops"] = c.get("gemm_flops", 0) + 2 * batch * M * Nn * K
+            # each operand once: broadcast (stride 0) operands count once for the batch
+            nb = (batch if sa else 1) * M * K * 2 + (batch if sb else 1) * K * Nn * 2
+            nb += batch * M * Nn * ((4 if C is not None else 0) + (4 if beta != 0 else 0) +
+                                    (2 if Cb is not None else 0))
+            c["gemm_bytes"] = c.get("gemm_bytes", 0) + nb
+            c["gemms"] = c.get("gemms", 0) + 1
 
 
 def field_params(seed, nr, nphi, r_in, r_out):
@@ -97,7 +109,11 @@ def field_params(seed, nr, nphi, r_in, r_out):
 class Surrogate:
     """Spectral neural operator on an nr x nphi grid (C5: 512 x 1024)."""
 
-    def __init__(self, nr=512, nphi=1024, r_in=0.1, r_out=5.0, G=1.0, batch=2, seed=0, device=None):
+    def __init__(self, nr=512, nphi=1024, r_in=0.1, r_out=5.0, G=1.0, batch=2, seed=0, device=None,
+                 modes_phi=M1, modes_r=K1):
+        if modes_r % 2 or not (2 <= modes_r <= nr) or not (1 <= modes_phi <= nphi // 2):
+            raise ValueError("modes_r must be even and <= nr, modes_phi <= nphi / 2")
+        self.M1, self.K1 = int(modes_phi), int(modes_r)
         self.dev = torch.device("cuda") if device is None else torch.device(device)
         if self.dev.index is None:
             self.dev = torch.device("cuda", torch.cuda.current_device())
@@ -122,7 +138,7 @@ class Surrogate:
         for l in range(4):
             self.P[f"W{l}"] = param((C, C), 1 / math.sqrt(C))
             self.P[f"b{l}"] = param((C,), 0.0)
-            sw = param((K1, M1, C, C, 2), 0.5 / C)
+            sw = param((self.K1, self.M1, C, C, 2), 0.5 / C)
             self.P[f"S{l}"] = sw
         for v in self.P.values():
             if v["b"] is not None:
@@ -138,13 +154,15 @@ class Surrogate:
         return out
 
     def _build_dft(self):
+        M1, K1 = self.M1, self.K1
         R, Pn = self.nr, self.nphi
         p = np.arange(Pn)
         m = np.arange(M1)
         ang = 2 * np.pi * np.outer(m, p) / Pn                        # [M1][P]
         Fphi = np.empty((2 * M1, Pn))
         Fphi[0::2], Fphi[1::2] = np.cos(ang) / Pn, -np.sin(ang) / Pn  # rows 2m (re), 2m+1 (im)
-        kv = np.concatenate([np.arange(16), np.arange(R - 16, R)])   # kept radial frequencies
+        h = K1 // 2
+        kv = np.concatenate([np.arange(h), np.arange(R - h, R)])     # kept radial frequencies
         r = np.arange(R)
         angr = 2 * np.pi * np.outer(kv, r) / R                       # [K1][R]
         Gr = np.concatenate([np.cos(angr), -np.sin(angr)]) / R       # [2 K1][R]
@@ -159,6 +177,7 @@ class Surrogate:
         self.HreT, self.HimT = self._bf(Hre.T), self._bf(Him.T)
 
     def _alloc(self):
+        M1, K1 = self.M1, self.K1
         B, R, Pn, n = self.B, self.nr, self.nphi, self.B * self.npix
         f32 = dict(dtype=torch.float32, device=self.dev)
         bf = dict(dtype=torch.bfloat16, device=self.dev)
@@ -201,6 +220,7 @@ class Surrogate:
 
     # ------------------------------------------------------------ forward
     def _spectral(self, l, v, pre):
+        M1, K1 = self.M1, self.K1
         k, B, R, Pn = self.k, self.B, self.nr, self.nphi
         k.gemm(B * R, 2 * M1, C, Pn, self.Fphi, Pn, 0, v, C, Pn * C, Cb=self.V1, ldc=C, sc=2 * M1 * C)
         k.gemm(B, 2 * K1, 2 * M1 * C, R, self.Gr, R, 0, self.V1, 2 * M1 * C, R * 2 * M1 * C, C=self.T,
@@ -242,6 +262,7 @@ class Surrogate:
         return self.WT
 
     def backward(self):
+        M1, K1 = self.M1, self.K1
         k, B, R, Pn, n = self.k, self.B, self.nr, self.nphi, self.B * self.npix
         k.call("sg_nn_cast", n * 2, _p(self.dout), _p(self.dout_b))
         self._wgrad(self.q, QH, self.dout_b, 2, "Q2")

@@ -27,14 +27,32 @@ def bf(t):
     return t.to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("batch,M,Nn,K,trans_a,alpha,beta,bias", [
+GEMM_CASES = [
     (1, 64, 64, 32, False, 1.0, 0.0, False), (3, 100, 70, 45, False, 0.5, 1.0, True),
     (2, 33, 130, 200, True, 1.0, 0.0, False), (5, 7, 2, 4096, True, 1.0, 0.5, True),
     (1, 1000, 32, 7, False, 1.0, 0.0, True),
     # 16-byte load paths (leading dimensions multiples of 8) with ragged tiles
     (2, 72, 40, 96, True, 1.0, 0.0, True), (1, 130, 24, 40, False, 2.0, 0.0, False),
-    (4, 64, 64, 64, False, 1.0, 1.0, True)])
-def test_gemm(batch, M, Nn, K, trans_a, alpha, beta, bias):
+    (4, 64, 64, 64, False, 1.0, 1.0, True),
+    # several 128-row and 128-column tiles, ragged in M, N and K; K = 16 (one
+    # product of a 64-deep step); the surrogate's azimuthal-DFT shape
+    (2, 300, 300, 136, False, 1.0, 0.0, True), (1, 257, 520, 72, True, 1.0, 1.0, False),
+    (3, 1024, 32, 16, False, 1.0, 0.0, False), (8, 32, 32, 1024, False, 1.0, 0.0, False)]
+
+
+@pytest.fixture(params=["tcgen05", "mma_sync"])
+def gemm_engine(request):
+    lib = N.load()
+    eng = {"tcgen05": N.SG_NN_GEMM_TCGEN05, "mma_sync": N.SG_NN_GEMM_MMA_SYNC}[request.param]
+    assert lib.sg_nn_set_gemm_engine(eng) == N.SG_OK
+    yield request.param
+    assert lib.sg_nn_set_gemm_engine(N.SG_NN_GEMM_TCGEN05) == N.SG_OK
+
+
+@pytest.mark.parametrize("batch,M,Nn,K,trans_a,alpha,beta,bias", GEMM_CASES)
+def test_gemm(gemm_engine, batch, M, Nn, K, trans_a, alpha, beta, bias):
+    """Both engines against float64 products of the same BF16 values; the
+    tcgen05 engine's device waits all completed (sg_nn_check)."""
     dev = torch.device("cuda:0")
     g = torch.Generator().manual_seed(M * 7 + K)
     A = torch.randn(batch, K, M, generator=g) if trans_a else torch.randn(batch, M, K, generator=g)
@@ -57,13 +75,48 @@ def test_gemm(batch, M, Nn, K, trans_a, alpha, beta, bias):
     got = Cd.double().cpu()
     assert (got - ref).abs().max() <= 1e-5 * ref.abs().max() * math.sqrt(K) + 1e-6
     assert torch.allclose(Cb.double().cpu(), got, rtol=1e-2, atol=1e-2 * ref.abs().max())
+    assert lib.sg_nn_check(None) == N.SG_OK
+
+
+@pytest.mark.parametrize("batch,M,Nn,K,beta", [(7, 32, 32, 1024, 0.0), (5, 48, 24, 200, 1.0),
+                                                (3, 130, 64, 72, 0.5), (6, 20, 40, 96, 0.0), (1, 64, 32, 256, 0.0)])
+def test_gemm_shared_a(gemm_engine, batch, M, Nn, K, beta):
+    """One A for the whole batch (stride 0) with K > 64: the tcgen05 engine
+    folds several batch entries into one 128-column tile (ragged last group,
+    N = 24 and 40 leaving tile columns unused)."""
+    dev = torch.device("cuda:0")
+    g = torch.Generator().manual_seed(batch * 1000 + K)
+    A = torch.randn(M, K, generator=g)
+    Bm = torch.randn(batch, K, Nn, generator=g)
+    C0 = torch.randn(batch, M, Nn, generator=g)
+    Ad, Bd = bf(A).to(dev), bf(Bm).to(dev)
+    Cd = C0.to(dev).contiguous()
+    Cb = torch.empty(batch, M, Nn, dtype=torch.bfloat16, device=dev)
+    lib = N.load()
+    vp = lambda t: t.data_ptr()
+    st = lib.sg_nn_gemm(batch, M, Nn, K, 1.0, vp(Ad), K, 0, 0, vp(Bd), Nn, K * Nn, beta, vp(Cd), Nn, M * Nn,
+                        vp(Cb), None, None)
+    assert st == 0
+    torch.cuda.synchronize()
+    ref = bf(A).double() @ bf(Bm).double() + beta * C0.double()
+    got = Cd.double().cpu()
+    assert (got - ref).abs().max() <= 1e-5 * ref.abs().max() * math.sqrt(K) + 1e-6
+    assert torch.allclose(Cb.double().cpu(), got, rtol=1e-2, atol=1e-2 * ref.abs().max())
+    assert lib.sg_nn_check(None) == N.SG_OK
+
+
+def test_gemm_engine_argument_checks():
+    lib = N.load()
+    assert lib.sg_nn_set_gemm_engine(2) == N.SG_ERR_ARG
+    assert lib.sg_nn_set_gemm_engine(-1) == N.SG_ERR_ARG
+    assert lib.sg_nn_set_gemm_engine(N.SG_NN_GEMM_TCGEN05) == N.SG_OK
 
 
 # ---------------------------------------------------------------- network
 def reference_loss(S):
     """The surrogate's forward pass and loss in float64 on the CPU (torch
     ops, autograd), from the model's own weights and DFT matrices."""
-    Bn, R, P, C, M1, K1 = S.B, S.nr, S.nphi, 32, 16, 32
+    Bn, R, P, C, M1, K1 = S.B, S.nr, S.nphi, 32, S.M1, S.K1
     n = Bn * R * P
     d = lambda t: t.detach().double().cpu()
     leaf = {}
@@ -105,9 +158,12 @@ def rel(a, b):
     return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
 
-def test_forward_and_gradients_match_reference():
+@pytest.mark.parametrize("modes_phi,modes_r", [(16, 32), (16, 16)])
+def test_forward_and_gradients_match_reference(modes_phi, modes_r):
+    """Both retained-mode sizes (16 azimuthal x 32 radial, and 16 x 16), with
+    every GEMM on the tcgen05 engine."""
     from paper_2506_10812_gb300.surrogate import Surrogate
-    S = Surrogate(nr=32, nphi=64, batch=2, seed=3)
+    S = Surrogate(nr=32, nphi=64, batch=2, seed=3, modes_phi=modes_phi, modes_r=modes_r)
     S.load([11, 12])
     S.forward()
     L, _ = S.loss(grad=True)
@@ -119,6 +175,7 @@ def test_forward_and_gradients_match_reference():
     for name, g in grads.items():
         got = S.P[name]["g"].double().cpu().reshape(g.shape)
         assert rel(got, g) < 1e-1, (name, rel(got, g))
+    assert N.load().sg_nn_check(None) == N.SG_OK
 
 
 def test_training_lowers_the_loss_and_gate():
