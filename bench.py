@@ -35,6 +35,7 @@ METRIC = "SG field cells/s and HBM roofline fraction at rel-L2<=1e-5 vs FP64 ora
 UNIT = "cells/s"
 L2_FLUSH_BYTES = 256 << 20
 PROFILE = os.path.join(ROOT, "profiles", "cols_2048x4096.md")
+BIFLUID_PROFILE = os.path.join(ROOT, "profiles", "cols_bifluid_2048x4096.md")
 BATCH_PROFILE = os.path.join(ROOT, "profiles", "batch_64discs.md")
 BATCH_STREAMS_PROFILE = os.path.join(ROOT, "profiles", "batch_streams_64discs.md")
 
@@ -174,11 +175,14 @@ def kernel_source_hash(names=("sg_kernels.cu", "sg_cols.cuh", "sg_cols_steps.cu"
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per column-pass launch from the committed ncu summary, if it
-    was taken on the current kernel source."""
+def profiled_traffic(args):
+    """DRAM bytes per column-pass launch from the committed ncu summary of this
+    workload (2048 x 4096, all three components, gas only or gas + dust), if
+    it was taken on the current kernel source."""
+    if args.engine != "fft32" or (args.nr, args.nphi) != (2048, 4096) or args.outputs != "phi,gr,gphi":
+        return None
     try:
-        txt = open(PROFILE).read()
+        txt = open(BIFLUID_PROFILE if args.bifluid else PROFILE).read()
     except OSError:
         return None
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
@@ -379,7 +383,7 @@ def run_ours(args):
     kname = "k_cols (fused column pass)" if args.engine == "fft32" else f"k_cols_mma ({args.engine} tensor-core DFT stages)"
     roofline = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic() if args.engine == "fft32" else None,
+                "traffic": profiled_traffic(args),
                 "peak_source": f"{peak_kind} HBM copy bandwidth", "algorithmic_bytes_per_launch": col_bytes}
     # the column pass against the FP32 arithmetic peak (it is issue-bound, so neither fraction saturates):
     # nominal 5 L log2 L flops per length-L transform and 8 L per source-kernel product, against
