@@ -420,3 +420,16 @@ def test_indirect_razor_thin_is_newtonian_star_pull():
         assert np.allclose(row, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max())
     # an axisymmetric disc pulls the star nowhere
     assert np.abs(oracle.indirect(g, 1.0 / R, h_g=0.05)).max() < 1e-12
+
+
+def test_fft64_threaded_equals_one_thread():
+    """The oracle timed on all host cores (scipy.fft workers) computes the
+    same FP64 transforms as its one-thread parity form: equal bits."""
+    d = inputs.ragged_noise(32, 64, offset=9, bifluid=True)
+    g = oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out)
+    plan = oracle.fft64_plan(g, h_g=d.h_g, h_d=d.h_d, G=d.G)
+    one = oracle.fft64_apply(plan, d.sigma_g, d.sigma_d)
+    many = oracle.fft64_apply(plan, d.sigma_g, d.sigma_d, workers=4)
+    assert set(one) == set(many)
+    for k in one:
+        assert np.array_equal(one[k], many[k]), k
