@@ -244,7 +244,8 @@ sg_status sg_direct_noalloc(const sg_params *p, const void *sigma_g, const void 
  * SG_ERR_ARG (NULL, a value outside the lists above), SG_ERR_UNSUPPORTED
  * (a direct-method plan, per-step staging of an FP64 plan, a staging whose
  * shared memory exceeds the device's per-block limit).  Batches' stream
- * engine and sg_batch_solve_loop launch with each plan's tiles.            */
+ * engine and sg_batch_solve_loop launch with each plan's tiles; a batch's
+ * captured graph keeps the tiles its plans had when it was created.       */
 enum { SG_COLS_STAGE_ALL = 0, SG_COLS_STAGE_STEP = 1 };
 typedef struct {
     int32_t rows_fwd;
@@ -422,7 +423,8 @@ sg_status sg_set_column_engine(sg_plan *plan, int32_t engine);
  * B [K][N] (ldb); C [M][N] (ldc) float and/or C_bf16 (same layout, bf16);
  * stride_* are batch strides in elements (0 broadcasts); bias float [N] or
  * NULL; beta != 0 needs C.  batch <= 65535, N <= 65535 x 128.
- * Engine (sg_nn_set_gemm_engine, process-wide): SG_NN_GEMM_TCGEN05 (default)
+ * Engine (sg_nn_set_gemm_engine, process-wide, read at each call; set it
+ * before calls are issued from several host threads): SG_NN_GEMM_TCGEN05 (default)
  * runs 128 x {32, 64, 128} tiles of tcgen05.mma with the accumulator in
  * tensor memory; SG_NN_GEMM_MMA_SYNC the warp-level m16n8k16 kernel, kept
  * for comparison.  Both sum K in the same 16-element groups but in a
