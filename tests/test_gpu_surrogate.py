@@ -105,6 +105,55 @@ def test_gemm_shared_a(gemm_engine, batch, M, Nn, K, beta):
     assert lib.sg_nn_check(None) == N.SG_OK
 
 
+def test_gemm_random_shapes(gemm_engine):
+    """40 seeded random shapes (M, N, K up to 700, batch up to 6, transposed
+    or not, shared or per-entry A, odd leading dimensions that force the
+    element-wise load paths) against float64 products of the same BF16
+    values."""
+    dev = torch.device("cuda:0")
+    lib = N.load()
+    rng = np.random.default_rng(2506)
+    vp = lambda t: t.data_ptr() if t is not None else None
+    for case in range(40):
+        batch = int(rng.integers(1, 7))
+        M, Nn, K = (int(x) for x in rng.integers(1, 700, 3))
+        if case % 4 == 0:
+            K = int(rng.integers(65, 700))            # several 64-deep steps
+        trans_a = bool(rng.integers(0, 2))
+        shared_a = bool(rng.integers(0, 2)) and not trans_a
+        if case % 5 == 0:
+            Nn = 8 * int(rng.integers(1, 9))         # batch folding candidates
+        pad = int(rng.integers(0, 3))                 # leading dimensions beyond the matrix
+        lda = (M if trans_a else K) + pad
+        ldb, ldc = Nn + pad, Nn + pad
+        g = torch.Generator().manual_seed(case)
+        rows_a = K if trans_a else M
+        A = torch.randn(1 if shared_a else batch, rows_a, lda, generator=g)
+        Bm = torch.randn(batch, K, ldb, generator=g)
+        C0 = torch.randn(batch, M, ldc, generator=g)
+        beta = float(rng.choice([0.0, 1.0, 0.5]))
+        bias = torch.randn(Nn, generator=g) if rng.integers(0, 2) else None
+        Ad, Bd = bf(A).to(dev), bf(Bm).to(dev)
+        Cd = C0.to(dev).contiguous()
+        st = lib.sg_nn_gemm(batch, M, Nn, K, 1.0, vp(Ad), lda, 0 if shared_a else rows_a * lda, int(trans_a),
+                            vp(Bd), ldb, K * ldb, beta, vp(Cd), ldc, M * ldc, None,
+                            vp(bias.to(dev)) if bias is not None else None, None)
+        assert st == 0, case
+        torch.cuda.synchronize()
+        Af = bf(A).double()[..., :M] if trans_a else bf(A).double()[..., :K]
+        opA = Af.transpose(1, 2) if trans_a else Af
+        if shared_a:
+            opA = opA.expand(batch, -1, -1)
+        ref = opA @ bf(Bm).double()[..., :Nn] + beta * C0.double()[..., :Nn]
+        if bias is not None:
+            ref = ref + bias.double()
+        got = Cd.double().cpu()
+        assert (got[..., :Nn] - ref).abs().max() <= 1e-5 * ref.abs().max() * math.sqrt(K) + 1e-6, case
+        # columns beyond N (the leading-dimension padding) are untouched
+        assert torch.equal(got[..., Nn:], C0.double()[..., Nn:]), case
+    assert lib.sg_nn_check(None) == N.SG_OK
+
+
 def test_gemm_engine_argument_checks():
     lib = N.load()
     assert lib.sg_nn_set_gemm_engine(2) == N.SG_ERR_ARG
