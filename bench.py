@@ -674,7 +674,9 @@ def run_direct(args):
     checked against the FP64 oracle on seeded targets; and the oracle's own
     direct sum on all host cores: full at 64 x 128, a seeded target sample at
     256 x 512 and at the 2048 x 4096 gas disc, extrapolated by targets (each
-    target's sum costs the same: all N sources)."""
+    target's sum costs the same: all N sources).  Beside them, the FFT path on
+    the same two discs: the GPU solve and the oracle's FP64 FFT convolution on
+    all host cores and on one."""
     import os
     import torch
     import oracle
@@ -735,6 +737,36 @@ def run_direct(args):
                                         "sample": ("full solve" if full else
                                                    f"{idx.size} seeded targets ({t_or:.1f} s), extrapolated "
                                                    f"by targets to all {n}")}
+        # the FFT path on the same disc: the GPU solve in the configuration's dtype, and the oracle's FP64 FFT
+        # convolution on all host cores and on one
+        fdt = torch.float64 if full else torch.float32
+        sg = torch.tensor(d.sigma_g, dtype=fdt, device=dev)
+        sd = None if d.sigma_d is None else torch.tensor(d.sigma_d, dtype=fdt, device=dev)
+        with Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, dtype=fdt, device=dev) as plan:
+            for _ in range(3):
+                plan.solve(sg, sd)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+            for a, e in ev:
+                a.record()
+                plan.solve(sg, sd)
+                e.record()
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(e) for a, e in ev) / len(ev)
+        per["gpu_fft"] = {"dtype": "f64" if full else "f32", "ms": ms, "cells_per_s": n / (ms * 1e-3), "steps": 20}
+        fplan = oracle.fft64_plan(g, d.h_g, d.h_d if d.sigma_d is not None else None, d.G)
+        tt = {}
+        for wk in (None, ncpu):
+            oracle.fft64_apply(fplan, d.sigma_g, d.sigma_d, workers=wk)
+            ts = []
+            for _ in range(5):
+                t0 = time.perf_counter()
+                oracle.fft64_apply(fplan, d.sigma_g, d.sigma_d, workers=wk)
+                ts.append(time.perf_counter() - t0)
+            tt[wk] = statistics.median(ts)
+        per["oracle_fft64"] = {"cells_per_s": n / tt[ncpu], "cores": ncpu, "seconds_per_solve": tt[ncpu],
+                               "single_core": {"cells_per_s": n / tt[None], "seconds_per_solve": tt[None]},
+                               "sample": "median of 5 solves (kernel spectra precomputed)"}
         lines[name] = per
     # the 2048 x 4096 gas disc: the oracle's direct sum on a target sample, extrapolated
     d3 = inputs.lognormal_gas(2048, 4096, offset=2)
@@ -769,7 +801,8 @@ def run_direct(args):
                            "note": "each pair evaluates the scaled Bessel pair K0e, K1e - K0e by branch (series, "
                                    "quadrature or asymptotic), so no fixed flop count per pair exists"},
               "gpu_launches": sum(v["steps"] * (2 if "gas + dust" in c else 1)
-                                  for c, per in lines.items() for k, v in per.items() if k in ("f32", "f64"))}
+                                  for c, per in lines.items() for k, v in per.items() if k in ("f32", "f64"))
+                              + sum(per["gpu_fft"]["steps"] * 3 for per in lines.values())}
     print(json.dumps(result), flush=True)
 
 
