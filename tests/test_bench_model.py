@@ -51,3 +51,30 @@ def test_outputs_option():
     for bad in ("", "gr,gr", "phi,xx"):
         with pytest.raises(SystemExit):
             bench.outputs_of(ns(bad))
+
+
+def test_profiled_traffic_matches_the_workload():
+    """The column pass's DRAM traffic comes from the ncu summary of the same
+    workload only: gas or gas + dust at 2048 x 4096 with all three components
+    on the FP32 FFT engine; any other size, output set or engine reports none.
+    Each committed summary carries the source hash it was captured on, and
+    the gas and gas + dust kernels differ, so the two figures differ."""
+    base = dict(engine="fft32", nr=2048, nphi=4096, outputs="phi,gr,gphi")
+    gas = bench.profiled_traffic(argparse.Namespace(bifluid=False, **base))
+    dust = bench.profiled_traffic(argparse.Namespace(bifluid=True, **base))
+    if gas is not None and dust is not None:
+        assert dust > gas
+    for change in (dict(nr=1024, nphi=2048), dict(outputs="gr,gphi"), dict(engine="tc_bf16x3")):
+        args = argparse.Namespace(bifluid=False, **dict(base, **change))
+        assert bench.profiled_traffic(args) is None
+
+
+def test_direct_mode_is_an_option():
+    import sys
+    argv = sys.argv
+    try:
+        sys.argv = ["bench.py", "--direct", "--steps", "3"]
+        args = bench.parse()
+    finally:
+        sys.argv = argv
+    assert args.direct and args.steps == 3 and not args.batch and not args.surrogate
