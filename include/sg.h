@@ -68,7 +68,8 @@ typedef enum {
 } sg_status;
 
 enum { SG_F32 = 0, SG_F64 = 1 };                  /* plan dtype                        */
-enum { SG_METHOD_FFT = 0, SG_METHOD_DIRECT = 1 };  /* App. C convolution / direct sum   */
+/* App. C convolution / direct sum / semi-spectral (FFT in phi, direct in r) */
+enum { SG_METHOD_FFT = 0, SG_METHOD_DIRECT = 1, SG_METHOD_SEMISPECTRAL = 2 };
 /* Ordered fluid pairs, source -> target (Sec. 2.2 names the four
  * combinations; pointwise K_gd = K_dg, but the lattice tables differ). */
 enum { SG_PAIR_GG = 0, SG_PAIR_GD = 1, SG_PAIR_DG = 2, SG_PAIR_DD = 3 };
@@ -77,17 +78,19 @@ enum { SG_COMP_PHI = 0, SG_COMP_R = 1, SG_COMP_AZ = 2 };
 #define SG_CHECK_FINITE 2u  /* flag: record NaN/Inf outputs, reported by sg_sync */
 
 typedef struct {
-    int32_t nr, nphi;        /* cells.  FFT method: powers of two, 8 <= nr <= 4096,
-                                32 <= nphi <= 8192.  DIRECT: nr >= 1, nphi >= 1    */
+    int32_t nr, nphi;        /* cells.  FFT and SEMISPECTRAL: powers of two,
+                                8 <= nr <= 4096, 32 <= nphi <= 8192.
+                                DIRECT: nr >= 1, nphi >= 1                          */
     double r_in, r_out;      /* radial cell edges, 0 < r_in < r_out                 */
     double h_g, h_d;         /* aspect ratios H^sg/r of gas and dust (> 0);
                                 h_d <= 0 means a gas-only disc                      */
-    const void *H_g_field;   /* DIRECT only, optional: device [nr][nphi] H_g^sg(r,phi)
-                                in the plan dtype (copied at create); NULL = h_g r  */
-    const void *H_d_field;   /* DIRECT only, optional, as above for dust            */
+    const void *H_g_field;   /* DIRECT and SEMISPECTRAL, optional: device [nr][nphi]
+                                H_g^sg(r,phi) in the plan dtype (copied at create);
+                                NULL = h_g r.  SEMISPECTRAL: every row constant    */
+    const void *H_d_field;   /* optional, as above for dust                         */
     double G;                /* gravitational constant (the paper's tests use 1)   */
     int32_t dtype;           /* SG_F32 or SG_F64                                    */
-    int32_t method;          /* SG_METHOD_FFT or SG_METHOD_DIRECT                   */
+    int32_t method;          /* SG_METHOD_FFT, _DIRECT or _SEMISPECTRAL              */
     uint32_t flags;          /* SG_CHECK_FINITE                                     */
 } sg_params;
 
@@ -96,7 +99,20 @@ typedef struct {
  * kernel depends on the grid and the aspect ratios only, so it is computed
  * once).  The build runs on `stream`; the call synchronises `stream` before
  * returning.  On success *out holds the plan (owned by the caller, release
- * with sg_destroy); on failure *out is NULL and nothing stays allocated.   */
+ * with sg_destroy); on failure *out is NULL and nothing stays allocated.
+ *
+ * SG_METHOD_SEMISPECTRAL (Sec. 5.2's route for a non-constant H/r: Fourier
+ * transform in phi, direct sum in r) takes scale heights that depend on r
+ * only, H_a(r) = h_a r or any positive field whose rows are constant
+ * (SG_ERR_ARG otherwise).  The pair kernel then depends on (r, r', phi - phi')
+ * and the direct sum is, per azimuthal mode m, one complex nr x nr matrix
+ * product.  The plan holds the phi-DFT of the exact pair kernel for every
+ * (fluid pair, component, m, r, r'): semi_table size = nsrc^2 x 3 x nphi/2 x
+ * nr^2 x (8 FP32 / 16 FP64), 25.8 GB for a 1024 x 2048 gas disc in FP32
+ * (SG_ERR_OOM when it does not fit), built from FP64 kernel samples and row
+ * transforms.  A solve is the FFT path's row transforms around one pass
+ * that streams the tables; its result is the direct sum's (the same finite
+ * sum, to the plan dtype's rounding).  sg_kernel_table is FFT only.        */
 sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream);
 
 /* Write the real-space lattice kernel of one ordered fluid pair and one

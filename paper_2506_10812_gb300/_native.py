@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libsg.so")
 SG_OK, SG_ERR_ARG, SG_ERR_UNSUPPORTED, SG_ERR_NOT_FFT_COMPATIBLE, SG_ERR_CUDA, SG_ERR_OOM, \
     SG_ERR_NONFINITE, SG_ERR_TIMEOUT = range(8)
 SG_F32, SG_F64 = 0, 1
-SG_METHOD_FFT, SG_METHOD_DIRECT = 0, 1
+SG_METHOD_FFT, SG_METHOD_DIRECT, SG_METHOD_SEMISPECTRAL = 0, 1, 2
 SG_PAIR_GG, SG_PAIR_GD, SG_PAIR_DG, SG_PAIR_DD = 0, 1, 2, 3
 SG_COMP_PHI, SG_COMP_R, SG_COMP_AZ = 0, 1, 2
 SG_CHECK_FINITE = 2

@@ -110,6 +110,7 @@ cudaError_t device_setup(int dev)
     cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     e = set_smem_limits(optin);
+    if (e == cudaSuccess) e = set_semi_smem_limits(optin);
     if (e == cudaSuccess) g_dev_ready[dev] = true;
     return e;
 }
@@ -266,6 +267,28 @@ sg_status solve_t(sg_plan *pl, const void *sg_, const void *sd_, void *const out
                                pl->tm_rows ? &pl->tm_oh : nullptr, sflag, !ev, pl->rows_inv);
         if (e != cudaSuccess) return cuda_fail(pl, e, "inverse row transform");
         if (ev) cudaEventRecord(pl->ev[3], s);
+    } else if (pl->p.method == SG_METHOD_SEMISPECTRAL) {
+        // the FFT path's row transforms around the per-mode radial products
+        e = launch_rows_fwd<R>((const R *)sg_, (const R *)sd_, pl->nsrc, pl->sh, nr, nphi, pl->tw_row,
+                               pl->twp_row, (const R *)pl->rcen, true, s, 0, -1, pl->tm_rows ? &pl->tm_sh : nullptr,
+                               sflag, pl->rows_fwd);
+        if (e != cudaSuccess) return cuda_fail(pl, e, "row transform");
+        if (ev) cudaEventRecord(pl->ev[1], s);
+        e = launch_semi_mv<R>(pl->sh, pl->tab, pl->oh, nr, nphi, pl->nsrc, mask, s);
+        if (e != cudaSuccess) return cuda_fail(pl, e, "radial products");
+        if (ev) cudaEventRecord(pl->ev[2], s);
+        RowOut ro{};
+        for (int q = 0; q < 6; ++q) {
+            if (!((mask >> q) & 1u)) continue;
+            ro.ptr[ro.n] = outs[q];
+            ro.src[ro.n] = q;
+            ro.is_phi[ro.n] = (q % 3) == SG_COMP_PHI;
+            ++ro.n;
+        }
+        e = launch_rows_inv<R>(pl->oh, ro, nr, nphi, pl->tw_row, pl->twp_row, (const R *)pl->rcen, flag, s, 0, -1,
+                               pl->tm_rows ? &pl->tm_oh : nullptr, sflag, false, pl->rows_inv);
+        if (e != cudaSuccess) return cuda_fail(pl, e, "inverse row transform");
+        if (ev) cudaEventRecord(pl->ev[3], s);
     } else {
         for (int b = 0; b < pl->nsrc; ++b) {
             if (!((mask >> (3 * b)) & 7u)) continue;
@@ -406,8 +429,9 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
         delete pl;
         return s;
     };
-    const bool fft = p->method == SG_METHOD_FFT;
-    if (p->method != SG_METHOD_FFT && p->method != SG_METHOD_DIRECT) return reject(SG_ERR_ARG, "unknown method");
+    const bool fft = p->method == SG_METHOD_FFT, semi = p->method == SG_METHOD_SEMISPECTRAL;
+    if (p->method != SG_METHOD_FFT && p->method != SG_METHOD_DIRECT && !semi)
+        return reject(SG_ERR_ARG, "unknown method");
     if (p->dtype != SG_F32 && p->dtype != SG_F64) return reject(SG_ERR_ARG, "unknown dtype");
     if (!(std::isfinite(p->r_in) && std::isfinite(p->r_out) && p->r_in > 0 && p->r_out > p->r_in))
         return reject(SG_ERR_ARG, "need 0 < r_in < r_out");
@@ -421,6 +445,10 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
             return reject(SG_ERR_NOT_FFT_COMPATIBLE, "the FFT method needs constant aspect ratios (no H fields)");
         if (!is_pow2(p->nr) || !is_pow2(p->nphi) || p->nr < 8 || p->nr > 4096 || p->nphi < 32 || p->nphi > 8192)
             return reject(SG_ERR_UNSUPPORTED, "FFT method: nr, nphi powers of two, 8<=nr<=4096, 32<=nphi<=8192");
+    } else if (semi) {
+        if (!is_pow2(p->nr) || !is_pow2(p->nphi) || p->nr < 8 || p->nr > 4096 || p->nphi < 32 || p->nphi > 8192)
+            return reject(SG_ERR_UNSUPPORTED,
+                          "semi-spectral method: nr, nphi powers of two, 8<=nr<=4096, 32<=nphi<=8192");
     } else if ((long long)p->nr * p->nphi > (1LL << 24)) {
         return reject(SG_ERR_UNSUPPORTED, "direct method limited to 2^24 cells");
     }
@@ -439,14 +467,51 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
         delete pl;
         return SG_ERR_CUDA;
     }
-    if (fft) {
+    if (fft || semi) {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, pl->device);
         const size_t need[] = {row_smem_bytes(p->nphi, row_rpc(p->nphi, pl->f64), pl->f64),
                                row_smem_bytes(p->nphi, row_rpc(p->nphi, true), true),
-                               col_smem_bytes(p->nr, pl->nsrc, pl->f64), tabcol_smem_bytes(pl->L, true)};
+                               fft ? col_smem_bytes(p->nr, pl->nsrc, pl->f64) : semi_mv_smem(p->nr, pl->nsrc, pl->f64),
+                               fft ? tabcol_smem_bytes(pl->L, true) : 0};
         for (size_t b : need)
             if (b > (size_t)optin) return reject(SG_ERR_UNSUPPORTED, "grid too large for shared memory in this dtype");
+    }
+    // semi-spectral: H fields must not depend on phi; their radial profiles build the tables
+    std::vector<double> Hprof[2];
+    if (semi) {
+        const size_t cells_h = (size_t)p->nr * p->nphi;
+        for (int a = 0; a < pl->nsrc; ++a) {
+            const void *fld = a == 0 ? p->H_g_field : p->H_d_field;
+            const double h = a == 0 ? p->h_g : p->h_d;
+            Hprof[a].resize(p->nr);
+            if (!fld) {
+                for (int i = 0; i < p->nr; ++i) Hprof[a][i] = h * p->r_in * std::exp((i + 0.5) * pl->du);
+                continue;
+            }
+            std::vector<double> hv(cells_h);
+            cudaError_t ce;
+            if (pl->f64) {
+                ce = cudaMemcpy(hv.data(), fld, cells_h * sizeof(double), cudaMemcpyDeviceToHost);
+            } else {
+                std::vector<float> hf(cells_h);
+                ce = cudaMemcpy(hf.data(), fld, cells_h * sizeof(float), cudaMemcpyDeviceToHost);
+                for (size_t k = 0; k < cells_h; ++k) hv[k] = hf[k];
+            }
+            if (ce != cudaSuccess) {
+                cudaGetLastError();
+                return reject(SG_ERR_ARG, "could not read an H field (device pointer of the plan dtype expected)");
+            }
+            for (int i = 0; i < p->nr; ++i) {
+                const double v = hv[(size_t)i * p->nphi];
+                if (!(std::isfinite(v) && v > 0))
+                    return reject(SG_ERR_ARG, "H fields must be finite and positive");
+                for (int j = 1; j < p->nphi; ++j)
+                    if (hv[(size_t)i * p->nphi + j] != v)
+                        return reject(SG_ERR_ARG, "the semi-spectral method needs H fields independent of phi");
+                Hprof[a][i] = v;
+            }
+        }
     }
     const size_t cells = (size_t)p->nr * p->nphi;
     std::vector<float> f;
@@ -467,7 +532,38 @@ sg_status sg_plan_create(sg_plan **out, const sg_params *p, void *stream)
     SG_TRY(cudaMalloc((void **)&pl->flag, sizeof(unsigned int)), "flag");
     SG_TRY(cudaMalloc((void **)&pl->ipart, (size_t)indirect_blocks(p->nphi) * 4 * sizeof(double)), "indirect sums");
     SG_TRY(cudaMemsetAsync(pl->flag, 0, sizeof(unsigned int), s), "flag");
-    if (fft) {
+    if (semi) {
+        SG_TRY(upload(&pl->tw_row64, twiddles<double>(p->nphi), s), "twiddles");
+        SG_TRY(upload(&pl->twp_row64, pass_twiddles<double>(p->nphi / 2), s), "twiddles");
+        if (pl->f64) {
+            pl->tw_row = pl->tw_row64;
+            pl->twp_row = pl->twp_row64;
+        } else {
+            SG_TRY(upload(&pl->tw_row, twiddles<float>(p->nphi), s), "twiddles");
+            SG_TRY(upload(&pl->twp_row, pass_twiddles<float>(p->nphi / 2), s), "twiddles");
+        }
+        const size_t cbytes = 2 * pl->esz;
+        SG_TRY(cudaMalloc(&pl->tab, semi_table_bytes(p->nr, p->nphi, pl->nsrc, pl->f64)), "semi-spectral tables");
+        SG_TRY(cudaMalloc(&pl->sh, (size_t)pl->nsrc * pl->N * p->nr * cbytes), "scratch");
+        SG_TRY(cudaMalloc(&pl->oh, (size_t)pl->nsrc * 3 * pl->N * p->nr * cbytes), "scratch");
+        encode_maps(pl);
+        if (p->H_g_field) {
+            SG_TRY(cudaMalloc(&pl->Hg, cells * pl->esz), "H_g copy");
+            SG_TRY(cudaMemcpyAsync(pl->Hg, p->H_g_field, cells * pl->esz, cudaMemcpyDeviceToDevice, s), "H_g copy");
+        }
+        if (p->H_d_field && pl->nsrc == 2) {
+            SG_TRY(cudaMalloc(&pl->Hd, cells * pl->esz), "H_d copy");
+            SG_TRY(cudaMemcpyAsync(pl->Hd, p->H_d_field, cells * pl->esz, cudaMemcpyDeviceToDevice, s), "H_d copy");
+        }
+        std::vector<double> rc(p->nr);
+        for (int i = 0; i < p->nr; ++i) rc[i] = p->r_in * std::exp((i + 0.5) * pl->du);
+        const double *hp[2] = {Hprof[0].data(), pl->nsrc == 2 ? Hprof[1].data() : nullptr};
+        SG_TRY(pl->f64 ? build_semi_tables<double>(p->nr, p->nphi, pl->nsrc, pl->du, pl->dphi, p->G, rc.data(), hp,
+                                                   pl->tab, pl->tw_row64, pl->twp_row64, s)
+                       : build_semi_tables<float>(p->nr, p->nphi, pl->nsrc, pl->du, pl->dphi, p->G, rc.data(), hp,
+                                                  pl->tab, pl->tw_row64, pl->twp_row64, s),
+               "semi-spectral table build");
+    } else if (fft) {
         SG_TRY(upload(&pl->tw_row64, twiddles<double>(p->nphi), s), "twiddles");
         SG_TRY(upload(&pl->twp_row64, pass_twiddles<double>(p->nphi / 2), s), "twiddles");
         SG_TRY(upload(&pl->twp_col64, pass_twiddles<double>(pl->L), s), "twiddles");
@@ -675,6 +771,7 @@ int32_t sg_launches_per_solve(const sg_plan *pl, uint32_t outmask)
     outmask &= allowed;
     if (!outmask) return 0;
     if (pl->p.method == SG_METHOD_FFT) return pl->engine ? 4 : 3;   // tensor-core engines: column 0 apart
+    if (pl->p.method == SG_METHOD_SEMISPECTRAL) return 3;
     return ((outmask & 7u) ? 1 : 0) + ((outmask & 0x38u) ? 1 : 0);
 }
 
@@ -723,7 +820,7 @@ sg_status sg_set_tiles(sg_plan *pl, const sg_tiles *t)
         return fail(pl, SG_ERR_ARG, "rows per CTA must be 2 or 4");
     if (t->cols_staging != SG_COLS_STAGE_ALL && t->cols_staging != SG_COLS_STAGE_STEP)
         return fail(pl, SG_ERR_ARG, "unknown column staging %d", t->cols_staging);
-    if (pl->p.method != SG_METHOD_FFT) return fail(pl, SG_ERR_UNSUPPORTED, "tiles apply to FFT plans");
+    if (pl->p.method == SG_METHOD_DIRECT) return fail(pl, SG_ERR_UNSUPPORTED, "tiles apply to FFT and semi-spectral plans");
     if (pl->f64 && t->cols_staging == SG_COLS_STAGE_STEP)
         return fail(pl, SG_ERR_UNSUPPORTED, "per-step column staging is FP32 only");
     int optin = 0;

@@ -131,6 +131,23 @@ cudaError_t launch_indirect(int nr, int nphi, int nsrc, const R *s0, const R *s1
                             double h0, double h1, const R *rcen, double G, double du, double dphi, double *partial,
                             double *out, cudaStream_t s);
 
+// Semi-spectral method (sg_semi.cu): tables of the phi-DFT of the exact pair
+// kernel for axisymmetric scale heights, [pair][component][nphi/2][nr][nr]
+// complex of type R (semi_table_bytes); rc_h, H_h[a]: host radial centres
+// and the source fluids' H profiles (FP64, nr each).  Synchronises `s`.
+size_t semi_table_bytes(int nr, int nphi, int nsrc, bool f64);
+template <typename R>
+cudaError_t build_semi_tables(int nr, int nphi, int nsrc, double du, double dphi, double G, const double *rc_h,
+                              const double *H_h[2], void *tab, const void *tw_row64, const void *twp_row64,
+                              cudaStream_t s);
+// The per-mode matrix-vector products: row spectra sh ([nsrc][nphi/2][nr])
+// -> column output oh ([nsrc * 3][nphi/2][nr]) for the outputs in outmask.
+template <typename R>
+cudaError_t launch_semi_mv(const void *sh, const void *tab, void *oh, int nr, int nphi, int nsrc, uint32_t outmask,
+                           cudaStream_t s);
+size_t semi_mv_smem(int nr, int nsrc, bool f64);
+cudaError_t set_semi_smem_limits(int max_optin);
+
 // Direct pair sum (general scale heights) for one target fluid.
 template <typename R>
 cudaError_t launch_direct(int nr, int nphi, double r_in, double du, double G, const R *sig_g,

@@ -26,8 +26,11 @@ class Plan:
     Parameters follow the paper's problem: ``nr`` x ``nphi`` log-polar cells
     between the radial edges ``r_in``, ``r_out``; aspect ratios ``h_g`` and
     (optional, bi-fluid) ``h_d``; gravitational constant ``G``.  ``method``
-    is ``"fft"`` (constant aspect ratios, App. C convolution) or ``"direct"``
-    (pair sum, optionally with scale-height fields ``H_g``, ``H_d``)."""
+    is ``"fft"`` (constant aspect ratios, App. C convolution), ``"direct"``
+    (pair sum, optionally with scale-height fields ``H_g``, ``H_d``) or
+    ``"semispectral"`` (Fourier transform in phi and direct sum in r, for
+    scale heights that depend on r only: ``H_g``, ``H_d`` with constant rows,
+    or the aspect ratios)."""
 
     def __init__(self, nr, nphi, r_in, r_out, h_g, h_d=None, G=1.0, dtype=torch.float32,
                  method="fft", H_g=None, H_d=None, check_finite=False, device=None):
@@ -58,7 +61,8 @@ class Plan:
                 setattr(p, name, H.data_ptr())
         p.G = self.G
         p.dtype = N.SG_F64 if dtype == torch.float64 else N.SG_F32
-        p.method = {"fft": N.SG_METHOD_FFT, "direct": N.SG_METHOD_DIRECT}[method]
+        p.method = {"fft": N.SG_METHOD_FFT, "direct": N.SG_METHOD_DIRECT,
+                    "semispectral": N.SG_METHOD_SEMISPECTRAL}[method]
         p.flags = N.SG_CHECK_FINITE if check_finite else 0
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

@@ -1,0 +1,170 @@
+"""GPU tests of the semi-spectral method (Fourier transform in phi, direct sum
+in r) for scale heights that depend on r only: with constant aspect ratios it
+reproduces the FFT path; with a flaring H(r) (the paper's App. D form,
+H/r = 0.05 r^p) it reproduces the oracle's direct sum with the same fields,
+whole grids in FP64 and FP32, sampled targets at 256 x 512; plus the
+argument checks and the entry points it shares with the other methods."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_10812_gb300 import _native as N
+from paper_2506_10812_gb300 import build as B
+from paper_2506_10812_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = (1e-5, 1e-4)
+TOL64 = (1e-11, 1e-11)
+ALPHA = 1e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    B.build()
+    N.load()
+    oracle.build()
+
+
+def rounded(a, dtype):
+    return a if dtype == torch.float64 else a.astype(np.float32).astype(np.float64)
+
+
+def grid(d):
+    return oracle.Grid(d.nr, d.nphi, d.r_in, d.r_out)
+
+
+def flaring(d, p=0.25, St=0.1):
+    """H_g = 0.05 r^(1 + p) and the dust's H_g sqrt(alpha / (alpha + St)),
+    both broadcast over phi ([nr][nphi])."""
+    R, _ = grid(d).mesh()
+    Hg = 0.05 * R ** (1.0 + p)
+    return Hg, Hg * np.sqrt(ALPHA / (ALPHA + St))
+
+
+def plan_of(d, dtype, method, H_g=None, H_d=None):
+    from paper_2506_10812_gb300 import Plan
+    dev = torch.device("cuda:0")
+    Hg = None if H_g is None else torch.tensor(H_g, dtype=dtype, device=dev)
+    Hd = None if H_d is None else torch.tensor(H_d, dtype=dtype, device=dev)
+    return Plan(d.nr, d.nphi, d.r_in, d.r_out, d.h_g, d.h_d, G=d.G, dtype=dtype, method=method, H_g=Hg, H_d=Hd,
+                device=dev)
+
+
+def solve(pl, d, dtype, outputs=("phi", "gr", "gphi")):
+    dev = torch.device("cuda:0")
+    sg = torch.tensor(rounded(d.sigma_g, dtype), dtype=dtype, device=dev)
+    sd = None if d.sigma_d is None else torch.tensor(rounded(d.sigma_d, dtype), dtype=dtype, device=dev)
+    out = pl.solve(sg, sd, outputs=outputs)
+    torch.cuda.synchronize()
+    return {k: v.double().cpu().numpy() for k, v in out.items()}
+
+
+def assert_close(out, ref, tol, label=""):
+    assert set(out) == set(ref), label
+    for k, v in out.items():
+        e2, em = oracle.rel_l2(v, ref[k]), oracle.rel_max(v, ref[k])
+        assert e2 <= tol[0] and em <= tol[1], f"{label} {k}: rel-L2 {e2:.3e} max {em:.3e}"
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+@pytest.mark.parametrize("bifluid", [False, True])
+def test_constant_aspect_ratio_matches_the_oracle_fft(dtype, tol, bifluid):
+    """H = h r: the semi-spectral sum is the FFT convolution's finite sum."""
+    d = inputs.spiral_bifluid(St=0.1, nr=64, nphi=128) if bifluid else inputs.small_gas()
+    with plan_of(d, dtype, "semispectral") as pl:
+        out = solve(pl, d, dtype)
+    ref = oracle.fft64(grid(d), rounded(d.sigma_g, dtype),
+                       None if d.sigma_d is None else rounded(d.sigma_d, dtype), h_g=d.h_g, h_d=d.h_d, G=d.G)
+    if dtype == torch.float32 and not bifluid:
+        # the nearly axisymmetric small disc: g_phi ~1e4 below g_r, FP32 floor ~1e-5 of its own norm
+        ref = {k: v for k, v in ref.items() if k != "gphi_g"}
+        out = {k: v for k, v in out.items() if k != "gphi_g"}
+    assert_close(out, ref, tol, f"semi h=const {dtype}")
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, TOL64), (torch.float32, TOL32)])
+@pytest.mark.parametrize("p", [0.125, 0.5])
+def test_flaring_disc_matches_the_direct_sum(dtype, tol, p):
+    """Gas + dust with H/r = 0.05 r^p (App. D's flaring forms) at 64 x 128:
+    every output element against the oracle's direct sum with the same H
+    fields, and against the GPU direct path."""
+    d = inputs.spiral_bifluid(St=0.1, nr=64, nphi=128)
+    Hg, Hd = flaring(d, p)
+    Hg, Hd = rounded(Hg, dtype), rounded(Hd, dtype)
+    ref = oracle.direct(grid(d), rounded(d.sigma_g, dtype), rounded(d.sigma_d, dtype), H_g=Hg, H_d=Hd, G=d.G)
+    with plan_of(d, dtype, "semispectral", Hg, Hd) as pl:
+        out = solve(pl, d, dtype)
+    assert_close(out, ref, tol, f"semi flaring p={p} {dtype}")
+    with plan_of(d, dtype, "direct", Hg, Hd) as pd:
+        od = solve(pd, d, dtype)
+    assert_close(out, od, (1e-12, 1e-12) if dtype == torch.float64 else tol, "semi vs GPU direct")
+
+
+def test_flaring_disc_256x512_sampled_targets():
+    """FP32 at 256 x 512 (gas + dust, St = 1, flaring p = 0.25): 512 seeded
+    targets plus the grid's corners and edges against the oracle's direct
+    sum."""
+    d = inputs.spiral_bifluid(St=1.0, nr=256, nphi=512)
+    Hg, Hd = flaring(d, 0.25, St=1.0)
+    Hg, Hd = rounded(Hg, torch.float32), rounded(Hd, torch.float32)
+    rng = np.random.default_rng(43)
+    idx = set(rng.choice(d.nr * d.nphi, 512, replace=False).tolist())
+    for i in (0, 1, d.nr // 2, d.nr - 1):
+        for j in (0, d.nphi // 2, d.nphi - 1):
+            idx.add(i * d.nphi + j)
+    idx = np.array(sorted(idx), dtype=np.int64)
+    ref = oracle.direct(grid(d), rounded(d.sigma_g, torch.float32), rounded(d.sigma_d, torch.float32),
+                        H_g=Hg, H_d=Hd, G=d.G, targets=idx)
+    with plan_of(d, torch.float32, "semispectral", Hg, Hd) as pl:
+        out = solve(pl, d, torch.float32)
+    assert_close({k: v.ravel()[idx] for k, v in out.items()}, ref, TOL32, "semi 256x512")
+
+
+def test_entry_points_and_checks():
+    """Output subsets, the host-buffer entry point, launch tiles, the indirect
+    term (equal to the direct plan's with the same fields) and the launch
+    count; a phi-dependent H field, a non-power-of-two grid and kernel-table
+    export are refused."""
+    from paper_2506_10812_gb300 import Plan
+    d = inputs.spiral_bifluid(St=0.1, nr=32, nphi=64)
+    Hg, Hd = flaring(d, 0.25)
+    dev = torch.device("cuda:0")
+    sg = torch.tensor(d.sigma_g, dtype=torch.float32, device=dev)
+    sd = torch.tensor(d.sigma_d, dtype=torch.float32, device=dev)
+    with plan_of(d, torch.float32, "semispectral", Hg, Hd) as pl:
+        full = {k: v.clone() for k, v in pl.solve(sg, sd).items()}
+        acc = pl.solve(sg, sd, outputs=("gr", "gphi"))
+        torch.cuda.synchronize()
+        for k, v in acc.items():
+            assert torch.equal(v, full[k]), k
+        host = pl.solve_host(sg.cpu(), sd.cpu())
+        for k, v in host.items():
+            assert torch.equal(torch.as_tensor(v), full[k].cpu()), k
+        pl.set_tiles(rows_fwd=2, rows_inv=4)
+        tiled = pl.solve(sg, sd)
+        torch.cuda.synchronize()
+        for k, v in tiled.items():
+            assert float((v - full[k]).norm() / full[k].norm()) <= 1e-6, k
+        assert pl.launches_per_solve() == 3
+        ab = pl.indirect(sg, sd).cpu()
+        with pytest.raises(N.SgError) as e:
+            pl.kernel_table()
+        assert e.value.status == N.SG_ERR_UNSUPPORTED
+    with plan_of(d, torch.float32, "direct", Hg, Hd) as pd:
+        ab_direct = pd.indirect(sg, sd).cpu()
+    assert torch.allclose(ab, ab_direct, rtol=1e-12, atol=0)
+    # H must not depend on phi
+    Hbad = Hg.copy()
+    Hbad[3, 5] *= 1.01
+    with pytest.raises(N.SgError) as e:
+        plan_of(d, torch.float32, "semispectral", Hbad, Hd)
+    assert e.value.status == N.SG_ERR_ARG
+    with pytest.raises(N.SgError) as e:
+        Plan(48, 64, d.r_in, d.r_out, d.h_g, d.h_d, method="semispectral", device=dev)
+    assert e.value.status == N.SG_ERR_UNSUPPORTED
+    lib = N.load()
+    assert lib.sg_launches_per_solve(None, 7) == 0
