@@ -130,8 +130,9 @@ k_semi_mv(const cplx<R> *__restrict__ sh, const cplx<R> *__restrict__ tab, cplx<
         const C *T = tab + ((size_t)((a * NS + b) * 3 + c) * N + m) * nr * nr;
         const C *sa = ss + a * nr;
         if constexpr (sizeof(R) == 4) {
-            // two complex per lane per step (16-byte loads; nr is even)
-#pragma unroll 2
+            // two complex per lane per step (16-byte loads; nr is even); four
+            // steps of four rows in flight per thread
+#pragma unroll 4
             for (int ip = 2 * lane; ip < nr; ip += 64) {
                 const float4 s = *reinterpret_cast<const float4 *>(sa + ip);
 #pragma unroll
