@@ -61,9 +61,15 @@ __device__ __forceinline__ void k0e_D_any<float>(float x, const BesselWeights &b
 }
 
 constexpr int DT = 256;   // targets per CTA and sources per shared-memory tile
+// FP32: compiled for 4 resident CTAs per SM (64 registers, a few spilled):
+// 256 x 512 gas + dust solve 708 -> 641 ms against the unbounded 94-register
+// build at 2 CTAs per SM (2 and 3 CTAs per SM: 754 and 751 ms); bit-identical.
+#ifndef SG_DIRECT_MINB
+#define SG_DIRECT_MINB 4
+#endif
 
 template <typename R>
-__global__ void __launch_bounds__(DT)
+__global__ void __launch_bounds__(DT, sizeof(R) == 4 ? SG_DIRECT_MINB : 1)
 k_direct(int nr, int nphi, R G, const R *__restrict__ sig_g, const R *__restrict__ sig_d,
          const R *__restrict__ Hg, const R *__restrict__ Hd, R h_g, R h_d, int tgt, R *phi, R *gr,
          R *gphi, const typename pair_of<R>::type *__restrict__ geo_i,
