@@ -168,3 +168,10 @@ def test_entry_points_and_checks():
     assert e.value.status == N.SG_ERR_UNSUPPORTED
     lib = N.load()
     assert lib.sg_launches_per_solve(None, 7) == 0
+    # batches bind FFT plans only
+    from paper_2506_10812_gb300 import Batch
+    with plan_of(d, torch.float32, "semispectral", Hg, Hd) as pl:
+        outs = {k: torch.empty((d.nr, d.nphi), device=dev) for k in ("phi_g", "gr_g", "gphi_g")}
+        with pytest.raises(N.SgError) as e:
+            Batch([pl], [sg], [sd], [outs])
+        assert e.value.status == N.SG_ERR_ARG
