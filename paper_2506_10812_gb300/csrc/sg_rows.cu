@@ -60,6 +60,14 @@ size_t row_smem_bytes(int nphi, int rpc, bool f64)
 #ifndef SG_ROWS_FWD_TMA
 #define SG_ROWS_FWD_TMA 1          // 0: forward rows by the load/store-unit transpose kernel
 #endif
+// The inverse rows store the solve's outputs as streaming (evict-first)
+// writes: nothing here reads them again, and they would otherwise push out of
+// L2 the column output that later CTAs still read.  Gas + dust 2048 x 4096
+// (six outputs, 201 MB of column output): inverse rows 92.4 -> 81.0 us,
+// solve 291 -> 277 us; the gas solve (three outputs) is unchanged.
+#ifndef SG_ROWS_INV_STREAM
+#define SG_ROWS_INV_STREAM 1
+#endif
 // Rows per CTA (NR, 2 or 4) is a per-plan choice (sg_set_tiles); the default
 // is 4 for the forward transform and 2 for the inverse (2048 x 4096 disc: the
 // inverse 51.0 -> 45.3 us with 2, the forward 27.2 -> 30.6 us; a shared-memory
@@ -451,7 +459,11 @@ k_rows_inv(const cplx<R> *__restrict__ oh, const __grid_constant__ RowOut o, int
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         v[e] = mkc<C>(v[e].x * sc, v[e].y * sc);   // (y[2n], y[2n+1])
+#if SG_ROWS_INV_STREAM
+        __stcs(&out[t + T * e], v[e]);
+#else
         out[t + T * e] = v[e];
+#endif
     }
     if (flag) {
         bool bad = false;
@@ -513,7 +525,11 @@ k_rows_inv_tma(const __grid_constant__ CUtensorMap tm, const __grid_constant__ R
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
         v[e] = make_float2(v[e].x * sc, v[e].y * sc);     // (y[2n], y[2n+1])
+#if SG_ROWS_INV_STREAM
+        __stcs(&out[t + T * e], v[e]);
+#else
         out[t + T * e] = v[e];
+#endif
     }
     if (flag) {
         bool bad = false;
