@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--sur-steps", type=int, default=5000, help="surrogate training steps (2 fields each)")
     ap.add_argument("--engine", default="fft32",
                     choices=("fft32", "dft_fp16x3", "dft_bf16x3", "dft_fp16", "dft_bf16", "tc_bf16x3", "tc_tf32x3",
-                             "tc_bf16"),
+                             "tc_bf16", "tc_fp16x3"),
                     help="column-pass engine (tensor-core DFT stages for the precision study; gas-only discs)")
     args = ap.parse_args()
     outputs_of(args)          # reject a bad --outputs before any device work

@@ -411,15 +411,17 @@ const char *sg_batch_last_error(const sg_batch *batch);
  * accumulate), with FP16 or BF16 operands split into high and low parts and
  * three products summed (..._X3), or a single product.
  * SG_ENGINE_TC_*: the radix-16 stages on the tcgen05 tensor cores (operands
- * in tensor and shared memory, FP32 accumulators in tensor memory): BF16 or
- * TF32 hi + lo operands with three products, or one BF16 product; the
- * length-2048 transforms' final radix-8 pass stays on CUDA cores.
+ * in tensor and shared memory, FP32 accumulators in tensor memory): BF16,
+ * TF32 or FP16 hi + lo operands with three products (FP16: each tile's
+ * operands scaled by a power of two into FP16's range), or one BF16 product;
+ * the length-2048 transforms' final radix-8 pass stays on CUDA cores.
  * All need an FP32 gas-only FFT plan with nr = 1024 or 2048
  * (SG_ERR_UNSUPPORTED otherwise); column 0 stays on the FP32 path.  The call
  * allocates a 4 KiB table on the first mma.sync engine and synchronises the
  * device; set it before capturing solves in a graph.  Batches ignore it.  */
 enum { SG_ENGINE_FFT32 = 0, SG_ENGINE_DFT_FP16X3 = 1, SG_ENGINE_DFT_BF16X3 = 2, SG_ENGINE_DFT_FP16 = 3,
-       SG_ENGINE_DFT_BF16 = 4, SG_ENGINE_TC_BF16X3 = 5, SG_ENGINE_TC_TF32X3 = 6, SG_ENGINE_TC_BF16 = 7 };
+       SG_ENGINE_DFT_BF16 = 4, SG_ENGINE_TC_BF16X3 = 5, SG_ENGINE_TC_TF32X3 = 6, SG_ENGINE_TC_BF16 = 7,
+       SG_ENGINE_TC_FP16X3 = 8 };
 sg_status sg_set_column_engine(sg_plan *plan, int32_t engine);
 
 /* ------------------------------------------------------------------------

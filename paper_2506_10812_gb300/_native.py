@@ -25,7 +25,7 @@ SG_COLS_STAGE_ALL, SG_COLS_STAGE_STEP = 0, 1
 SG_ENGINE_FFT32, SG_ENGINE_DFT_FP16X3, SG_ENGINE_DFT_BF16X3, SG_ENGINE_DFT_FP16, SG_ENGINE_DFT_BF16, \
     SG_ENGINE_TC_BF16X3, SG_ENGINE_TC_TF32X3, SG_ENGINE_TC_BF16 = range(8)
 ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf16": 4,
-           "tc_bf16x3": 5, "tc_tf32x3": 6, "tc_bf16": 7}
+           "tc_bf16x3": 5, "tc_tf32x3": 6, "tc_bf16": 7, "tc_fp16x3": 8}
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",

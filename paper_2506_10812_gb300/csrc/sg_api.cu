@@ -778,7 +778,8 @@ int32_t sg_launches_per_solve(const sg_plan *pl, uint32_t outmask)
 sg_status sg_set_column_engine(sg_plan *pl, int32_t engine)
 {
     if (!pl) return SG_ERR_ARG;
-    if (engine < SG_ENGINE_FFT32 || engine > SG_ENGINE_TC_BF16) return fail(pl, SG_ERR_ARG, "unknown engine %d", engine);
+    if (engine < SG_ENGINE_FFT32 || engine > SG_ENGINE_TC_FP16X3)
+        return fail(pl, SG_ERR_ARG, "unknown engine %d", engine);
     if (engine == SG_ENGINE_FFT32) {
         pl->engine = 0;
         return SG_OK;

@@ -28,9 +28,16 @@
 //          value), lo = the same of x - hi; kind::tf32; the same three
 //          products;
 //   MODE 3 (BF16 x1): bf16(x) bf16(B), one product.
-// BF16 and TF32 keep FP32's 8-bit exponent, so no operand needs scaling.
+//   MODE 4 (FP16 x3): as MODE 1 in FP16 (11 significand bits per part, so
+//          22 in all), kind::f16 with F16 A and B.  FP16's 5-bit exponent
+//          needs the operands scaled: each 128-butterfly tile multiplies its
+//          inputs by the power of two that brings the tile's largest
+//          magnitude into (1/2, 1] (a tile-wide max through the tile's
+//          named barrier) and divides the products by it, exactly.
+// BF16 and TF32 keep FP32's 8-bit exponent, so those need no scaling.
 // The length-2048 transform's final radix-8 pass stays on the CUDA cores.
 // Column 0 (the packed real pair) stays on the FP32 column pass.
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include "sg_cols.cuh"
@@ -62,6 +69,7 @@ __device__ constexpr double kCos16[16] = {1.0,
 
 template <int MODE> struct TcMode {
     static constexpr bool tf32 = MODE == 2;
+    static constexpr bool f16 = MODE == 4;
     static constexpr bool split = MODE != 3;
     static constexpr int esz = tf32 ? 4 : 2;          // operand bytes
     static constexpr int aw = 32 * esz / 4;           // tensor-memory columns of one 32-wide operand row
@@ -69,7 +77,7 @@ template <int MODE> struct TcMode {
     static constexpr int tile_cols = 2 * aw + 32;     // A hi, A lo, D (FP32)
     static constexpr int bbytes = 32 * 32 * esz;      // one B matrix
     static constexpr unsigned lbo = 128, sbo = 4 * 128 * (esz == 2 ? 1 : 2);
-    static constexpr uint32_t idesc = umma_idesc(128, 32, tf32 ? 2u : 1u);
+    static constexpr uint32_t idesc = umma_idesc(128, 32, tf32 ? 2u : f16 ? 0u : 1u);
 };
 
 __host__ __device__ constexpr int tc_tiles(int L) { return L / 16 / 128; }
@@ -102,6 +110,8 @@ struct TcState {
     unsigned phase;              // its next phase parity
     unsigned int *flag;
     int failed;                  // a completion wait gave up (uniform across the CTA)
+    float *wmax;                 // FP16 mode: the warps' largest magnitudes, 4 per tile
+    float unscale;               // FP16 mode: this transform stage's inverse scale
 };
 
 template <int L, int MODE, bool FWD> struct TcDft16 {
@@ -130,6 +140,32 @@ template <int L, int MODE, bool FWD> struct TcDft16 {
                 tmem_st16u(s.a_hi + 16 * h, hi);
                 tmem_st16u(s.a_lo + 16 * h, lo);
             }
+        } else if constexpr (M::f16) {
+            // the tile's power-of-two scale: its largest magnitude into (1/2, 1]
+            float mx = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) mx = fmaxf(mx, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const int tl = t >> 7, w4 = (t >> 5) & 3;
+            if ((t & 31) == 0) s.wmax[4 * tl + w4] = mx;
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + tl) : "memory");
+            mx = fmaxf(fmaxf(s.wmax[4 * tl], s.wmax[4 * tl + 1]), fmaxf(s.wmax[4 * tl + 2], s.wmax[4 * tl + 3]));
+            int ex = 0;
+            if (mx > 0.f && isfinite(mx)) frexpf(mx, &ex);   // mx = f 2^ex, f in [1/2, 1)
+            const float sc = ldexpf(1.f, -ex), isc = ldexpf(1.f, ex);
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float xr = v[j].x * sc, xi = v[j].y * sc;
+                const __half2 h = __floats2half2_rn(xr, xi);
+                const __half2 l = __floats2half2_rn(xr - __low2float(h), xi - __high2float(h));
+                hi[j] = *reinterpret_cast<const uint32_t *>(&h);
+                lo[j] = *reinterpret_cast<const uint32_t *>(&l);
+            }
+            tmem_st16u(s.a_hi, hi);
+            tmem_st16u(s.a_lo, lo);
+            s.unscale = isc;
         } else {
             uint32_t hi[16], lo[16];
 #pragma unroll
@@ -177,6 +213,10 @@ template <int L, int MODE, bool FWD> struct TcDft16 {
         s.failed = __syncthreads_or(!ok) || s.failed;
         tmem_fence_after();
         if (!s.failed) tmem_ld16c(s.d, v);
+        if constexpr (M::f16) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = make_float2(v[j].x * s.unscale, v[j].y * s.unscale);
+        }
     }
 };
 
@@ -238,6 +278,10 @@ k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 
             const uint32_t h = __float_as_uint((float)val) & 0xFFFFE000u;
             const uint32_t l = __float_as_uint((float)(val - (double)__uint_as_float(h))) & 0xFFFFE000u;
             *reinterpret_cast<uint32_t *>(dst) = lo ? l : h;
+        } else if constexpr (M::f16) {
+            const __half h = __double2half(val);
+            const __half l = __double2half(val - (double)__half2float(h));
+            *reinterpret_cast<__half *>(dst) = lo ? l : h;
         } else {
             const uint32_t h = bf16_bits((float)val);
             const uint32_t l = bf16_bits((float)(val - (double)__uint_as_float(h << 16)));
@@ -261,6 +305,8 @@ k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 
     st.phase = 0;
     st.flag = flag;
     st.failed = 0;
+    st.wmax = reinterpret_cast<float *>(smem_tc + 64);   // 4 per tile, in the header
+    st.unscale = 1.f;
     cols_pair_steps<float, L, 1>(sh, tab, oh, L / 2, N, outmask, tw, flag, xb, tb, bar, m, 0,
                                  TcEngine<L, MODE>{&st});
     // every thread's tensor-memory accesses precede the release
@@ -298,6 +344,7 @@ cudaError_t launch_cols_tc(int engine, const void *sh, const void *tab, void *oh
     switch (engine) {
     case SG_ENGINE_TC_BF16X3: SG_GO(1);
     case SG_ENGINE_TC_TF32X3: SG_GO(2);
+    case SG_ENGINE_TC_FP16X3: SG_GO(4);
     default: SG_GO(3);
     }
 #undef SG_GO

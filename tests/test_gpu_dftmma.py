@@ -89,13 +89,14 @@ def test_fp16x3_full_size():
         assert e2 <= TOL32[0] and em <= TOL32[1], (k, e2, em)
 
 
-@pytest.mark.parametrize("engine", ["tc_bf16x3", "tc_tf32x3"])
+@pytest.mark.parametrize("engine", ["tc_bf16x3", "tc_tf32x3", "tc_fp16x3"])
 def test_tcgen05_split_engines_meet_fp32_tolerance(disc_1024, engine):
     """tcgen05 engines (each radix-16 DFT one tensor-core product per
     128-butterfly tile: operands in tensor and shared memory, FP32
-    accumulators in tensor memory; BF16 or TF32 hi + lo operands, three
-    products): the FP32 tolerance against the FP64 oracle at 1024 x 2048
-    (column length 2048: two radix-16 stages on the tensor cores)."""
+    accumulators in tensor memory; BF16, TF32 or FP16 (per-tile power-of-two
+    scaling) hi + lo operands, three products): the FP32 tolerance against
+    the FP64 oracle at 1024 x 2048 (column length 2048: two radix-16 stages
+    on the tensor cores)."""
     d, ref = disc_1024
     err = errors(solve(d, engine), ref)
     for k, (e2, em) in err.items():
@@ -111,7 +112,7 @@ def test_tcgen05_single_product_is_worse(disc_1024):
     assert single > 10 * split, (single, split)
 
 
-@pytest.mark.parametrize("engine", ["tc_bf16x3", "tc_tf32x3"])
+@pytest.mark.parametrize("engine", ["tc_bf16x3", "tc_tf32x3", "tc_fp16x3"])
 def test_tcgen05_full_size(engine):
     """2048 x 4096 (column length 4096: all three radix-16 stages on the
     tensor cores, two 128-butterfly tiles per product)."""
