@@ -424,6 +424,16 @@ enum { SG_ENGINE_FFT32 = 0, SG_ENGINE_DFT_FP16X3 = 1, SG_ENGINE_DFT_BF16X3 = 2, 
        SG_ENGINE_TC_FP16X3 = 8 };
 sg_status sg_set_column_engine(sg_plan *plan, int32_t engine);
 
+/* One radix-16 stage of a tcgen05 engine alone, for testing it against a
+ * plain DFT: `count` independent 16-point DFTs (a positive multiple of 256)
+ * of the complex FP32 sequences in[16 q .. 16 q + 15] (interleaved re, im;
+ * caller-owned device memory) into out (same layout, natural order),
+ * X[k] = sum_n x[n] exp(-+ 2 pi i n k / 16) (inverse: +, unnormalised).
+ * engine: SG_ENGINE_TC_*.  A CTA runs 256 DFTs (two tensor-core tiles) with
+ * the column engine's own operand split, scaling, products and bounded
+ * waits.  Errors: SG_ERR_ARG (engine, count, NULL), SG_ERR_CUDA.  Async.   */
+sg_status sg_tc_dft16(int32_t engine, int64_t count, const void *in, void *out, int32_t inverse, void *stream);
+
 /* ------------------------------------------------------------------------
  * Kernels of the spectral neural-operator surrogate of the field solve
  * (paper_2506_10812_gb300/surrogate.py builds a 4-layer, width-32 spectral

@@ -29,7 +29,7 @@ ENGINES = {"fft32": 0, "dft_fp16x3": 1, "dft_bf16x3": 2, "dft_fp16": 3, "dft_bf1
 
 # Every symbol include/sg.h declares (checked by the ABI test).
 EXPORTS = ("sg_plan_create", "sg_kernel_table", "sg_potential", "sg_accel", "sg_solve",
-           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_set_column_engine", "sg_get_tiles", "sg_set_tiles", "sg_batch_create", "sg_batch_solve",
+           "sg_solve_host", "sg_indirect", "sg_sync", "sg_set_stage_events", "sg_stage_times", "sg_launches_per_solve", "sg_direct_noalloc", "sg_set_column_engine", "sg_tc_dft16", "sg_get_tiles", "sg_set_tiles", "sg_batch_create", "sg_batch_solve",
            "sg_batch_solve_loop", "sg_batch_release", "sg_batch_sync", "sg_batch_config", "sg_batch_tune_results", "sg_batch_tile_trials", "sg_batch_destroy",
            "sg_batch_last_error", "sg_nn_set_gemm_engine", "sg_nn_check", "sg_nn_gemm", "sg_nn_spec_combine", "sg_nn_spec_combine_bwd", "sg_nn_modemix",
            "sg_nn_modemix_bwd", "sg_nn_act", "sg_nn_act_bwd", "sg_nn_colsum", "sg_nn_rel_l2", "sg_nn_adam", "sg_nn_cast",
@@ -124,6 +124,8 @@ def load() -> ctypes.CDLL:
     lib.sg_batch_last_error.restype = ctypes.c_char_p
     lib.sg_set_column_engine.argtypes = [vp, i32]
     lib.sg_set_column_engine.restype = st
+    lib.sg_tc_dft16.argtypes = [i32, ctypes.c_int64, vp, vp, i32, vp]
+    lib.sg_tc_dft16.restype = st
     lib.sg_get_tiles.argtypes = [vp, ctypes.POINTER(SgTiles)]
     lib.sg_get_tiles.restype = st
     lib.sg_set_tiles.argtypes = [vp, ctypes.POINTER(SgTiles)]

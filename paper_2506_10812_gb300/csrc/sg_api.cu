@@ -837,6 +837,17 @@ sg_status sg_set_tiles(sg_plan *pl, const sg_tiles *t)
     return SG_OK;
 }
 
+sg_status sg_tc_dft16(int32_t engine, int64_t count, const void *in, void *out, int32_t inverse, void *stream)
+{
+    if (engine < SG_ENGINE_TC_BF16X3 || engine > SG_ENGINE_TC_FP16X3 || count < 256 || count % 256 ||
+        count / 256 > 0x7FFFFFFF || !in || !out)
+        return SG_ERR_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = launch_tc_stage(engine, in, out, count, inverse ? 1 : 0, (cudaStream_t)stream);
+    return e == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
 void sg_destroy(sg_plan *pl)
 {
     if (!pl) return;

@@ -93,6 +93,9 @@ size_t cols_mma_smem(int nr);
 // 2 nr in {2048, 4096}; engine SG_ENGINE_TC_*.
 cudaError_t launch_cols_tc(int engine, const void *sh, const void *tab, void *oh, int nr, int nphi, uint32_t outmask,
                            const void *tw_col, unsigned int *flag, cudaStream_t s);
+// One radix-16 stage alone on the tcgen05 engine `engine`: count 16-point
+// DFTs (a multiple of 256) of in -> out, natural order (sg_tc_dft16).
+cudaError_t launch_tc_stage(int engine, const void *in, void *out, long long count, int inverse, cudaStream_t s);
 // Host: the 8 x 32 x 4 A-fragment words (FP16 if f16, else BF16).
 void dftmma_frag_table(bool f16, uint32_t *out);
 

@@ -242,22 +242,18 @@ template <int L, int MODE> constexpr size_t tc_smem_request()
     return tc_smem_bytes<L, MODE>() > floor_bytes ? tc_smem_bytes<L, MODE>() : floor_bytes;
 }
 
+// Per-CTA set-up of the tensor-core butterflies: the tensor-memory
+// allocation, the B matrices in shared memory (from smem_tc + 1024), the
+// product-completion mbarriers and the state of each thread's tile.
 template <int L, int MODE>
-__global__ void __launch_bounds__(L / 16, L == 4096 ? 2 : 3)
-k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 *__restrict__ oh, int N,
-          uint32_t outmask, const float2 *__restrict__ tw, unsigned int *flag)
+__device__ __forceinline__ void tc_setup(unsigned char *smem_tc, TcState &st, unsigned int *flag)
 {
     using M = TcMode<MODE>;
-    extern __shared__ __align__(1024) unsigned char smem_tc[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_tc);          // staged kernel spectra
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_tc + 16);    // product completion, one per tile
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem_tc + 48);
     unsigned char *bmat = smem_tc + 1024;
-    float2 *xb = reinterpret_cast<float2 *>(bmat + 4 * M::bbytes);
-    float2 *tb = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(xb) +
-                                            ((((size_t)padded_len(L) * 8) + 15) & ~(size_t)15));
     constexpr int T = L / 16, NCOLS = tc_tmem_cols<L, MODE>();
-    const int t = threadIdx.x, m = blockIdx.x + 1;
+    const int t = threadIdx.x;
     if (t < 32) {
         tmem_alloc(tslot, NCOLS);
         tmem_relinquish();
@@ -293,7 +289,6 @@ k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    TcState st;
     st.tbase = *tslot;
     const int tile = t >> 7;
     const uint32_t lane = (uint32_t)(32 * ((t >> 5) & 3)) << 16;
@@ -307,13 +302,54 @@ k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 
     st.failed = 0;
     st.wmax = reinterpret_cast<float *>(smem_tc + 64);   // 4 per tile, in the header
     st.unscale = 1.f;
-    cols_pair_steps<float, L, 1>(sh, tab, oh, L / 2, N, outmask, tw, flag, xb, tb, bar, m, 0,
-                                 TcEngine<L, MODE>{&st});
-    // every thread's tensor-memory accesses precede the release
+}
+
+// Release the CTA's tensor memory once every thread's accesses are done.
+template <int L, int MODE> __device__ __forceinline__ void tc_teardown(const TcState &st)
+{
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
-    if (t < 32) tmem_dealloc(st.tbase, NCOLS);
+    if (threadIdx.x < 32) tmem_dealloc(st.tbase, tc_tmem_cols<L, MODE>());
+}
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(L / 16, L == 4096 ? 2 : 3)
+k_cols_tc(const float2 *__restrict__ sh, const float2 *__restrict__ tab, float2 *__restrict__ oh, int N,
+          uint32_t outmask, const float2 *__restrict__ tw, unsigned int *flag)
+{
+    using M = TcMode<MODE>;
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_tc);          // staged kernel spectra
+    float2 *xb = reinterpret_cast<float2 *>(smem_tc + 1024 + 4 * M::bbytes);
+    float2 *tb = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(xb) +
+                                            ((((size_t)padded_len(L) * 8) + 15) & ~(size_t)15));
+    const int m = blockIdx.x + 1;
+    TcState st;
+    tc_setup<L, MODE>(smem_tc, st, flag);
+    cols_pair_steps<float, L, 1>(sh, tab, oh, L / 2, N, outmask, tw, flag, xb, tb, bar, m, 0,
+                                 TcEngine<L, MODE>{&st});
+    tc_teardown<L, MODE>(st);
+}
+
+// One radix-16 stage alone: 256 threads per CTA each run one 16-point DFT of
+// in[16 (256 blockIdx.x + t) ..] (natural order) on the tensor cores into out.
+template <int MODE>
+__global__ void __launch_bounds__(256, 2)
+k_tc_stage(const float2 *__restrict__ in, float2 *__restrict__ out, int inverse, unsigned int *flag)
+{
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    TcState st;
+    tc_setup<4096, MODE>(smem_tc, st, flag);
+    const size_t base = ((size_t)blockIdx.x * 256 + threadIdx.x) * 16;
+    float2 v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = in[base + j];
+    if (inverse) TcDft16<4096, MODE, false>{&st}(v);
+    else TcDft16<4096, MODE, true>{&st}(v);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) out[base + j] = v[j];
+    tc_teardown<4096, MODE>(st);
 }
 
 template <int L, int MODE>
@@ -329,7 +365,26 @@ cudaError_t go_tc(const void *sh, const void *tab, void *oh, int nphi, uint32_t 
     return cudaGetLastError();
 }
 
+template <int MODE> cudaError_t go_stage(const void *in, void *out, long long count, int inverse, cudaStream_t s)
+{
+    const size_t smem = tc_smem_request<4096, MODE>();
+    cudaError_t e = cudaFuncSetAttribute(k_tc_stage<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tc_stage<MODE><<<(unsigned)(count / 256), 256, smem, s>>>((const float2 *)in, (float2 *)out, inverse, nullptr);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_tc_stage(int engine, const void *in, void *out, long long count, int inverse, cudaStream_t s)
+{
+    switch (engine) {
+    case SG_ENGINE_TC_BF16X3: return go_stage<1>(in, out, count, inverse, s);
+    case SG_ENGINE_TC_TF32X3: return go_stage<2>(in, out, count, inverse, s);
+    case SG_ENGINE_TC_FP16X3: return go_stage<4>(in, out, count, inverse, s);
+    default: return go_stage<3>(in, out, count, inverse, s);
+    }
+}
 
 cudaError_t launch_cols_tc(int engine, const void *sh, const void *tab, void *oh, int nr, int nphi, uint32_t outmask,
                            const void *tw_col, unsigned int *flag, cudaStream_t s)

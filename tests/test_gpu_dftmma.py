@@ -141,3 +141,50 @@ def test_engine_argument_checks():
         with pytest.raises(N.SgError) as ei:
             plan.set_column_engine("dft_fp16")
         assert ei.value.status == N.SG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("engine,tol", [("tc_bf16x3", 5e-5), ("tc_tf32x3", 5e-6), ("tc_fp16x3", 5e-6),
+                                        ("tc_bf16", None)])
+@pytest.mark.parametrize("inverse", [False, True])
+def test_tcgen05_single_stage_against_fp64_dft(engine, tol, inverse):
+    """One radix-16 stage of each tcgen05 engine alone (sg_tc_dft16): 4096
+    seeded 16-point DFTs against float64 DFTs.  Each 128-DFT tile (one
+    tensor-core product) has its own magnitude, the 32 tiles spanning six
+    decades, which exercises the FP16 engine's per-tile scaling; the error
+    of each output sequence is measured against its own largest value.  The
+    single BF16 product is orders of magnitude worse than the split
+    engines."""
+    import ctypes
+    lib = N.load()
+    rng = np.random.default_rng(1606)
+    count = 4096
+    mag = np.repeat(10.0 ** rng.uniform(-3, 3, (count // 128, 1)), 128, axis=0)
+    x = (rng.standard_normal((count, 16)) + 1j * rng.standard_normal((count, 16))) * mag
+    xin = torch.tensor(np.stack([x.real, x.imag], -1).astype(np.float32), device="cuda:0").contiguous()
+    out = torch.empty_like(xin)
+    st = lib.sg_tc_dft16(N.ENGINES[engine], count, ctypes.c_void_p(xin.data_ptr()),
+                         ctypes.c_void_p(out.data_ptr()), int(inverse), None)
+    assert st == N.SG_OK
+    torch.cuda.synchronize()
+    xr = xin.double().cpu().numpy()
+    z = xr[..., 0] + 1j * xr[..., 1]
+    ref = np.fft.ifft(z, axis=1) * 16 if inverse else np.fft.fft(z, axis=1)
+    o = out.double().cpu().numpy()
+    got = o[..., 0] + 1j * o[..., 1]
+    err = float(np.max(np.abs(got - ref).max(axis=1) / np.abs(ref).max(axis=1)))
+    if tol is None:
+        assert err > 1e-3, err
+    else:
+        assert err <= tol, (engine, err)
+
+
+def test_tcgen05_single_stage_argument_checks():
+    import ctypes
+    lib = N.load()
+    buf = torch.empty(256 * 16 * 2, device="cuda:0")
+    p = ctypes.c_void_p(buf.data_ptr())
+    assert lib.sg_tc_dft16(N.ENGINES["fft32"], 256, p, p, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(N.ENGINES["dft_fp16x3"], 256, p, p, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 100, p, p, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 0, p, p, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 256, None, p, 0, None) == N.SG_ERR_ARG
