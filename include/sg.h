@@ -427,11 +427,13 @@ sg_status sg_set_column_engine(sg_plan *plan, int32_t engine);
 /* One radix-16 stage of a tcgen05 engine alone, for testing it against a
  * plain DFT: `count` independent 16-point DFTs (a positive multiple of 256)
  * of the complex FP32 sequences in[16 q .. 16 q + 15] (interleaved re, im;
- * caller-owned device memory) into out (same layout, natural order),
+ * caller-owned device memory, 8-byte aligned) into out (same layout,
+ * natural order; a separate buffer that does not overlap in),
  * X[k] = sum_n x[n] exp(-+ 2 pi i n k / 16) (inverse: +, unnormalised).
  * engine: SG_ENGINE_TC_*.  A CTA runs 256 DFTs (two tensor-core tiles) with
  * the column engine's own operand split, scaling, products and bounded
- * waits.  Errors: SG_ERR_ARG (engine, count, NULL), SG_ERR_CUDA.  Async.   */
+ * waits.  Errors: SG_ERR_ARG (engine, count, NULL, alignment, overlap),
+ * SG_ERR_CUDA.  Async.                                                     */
 sg_status sg_tc_dft16(int32_t engine, int64_t count, const void *in, void *out, int32_t inverse, void *stream);
 
 /* ------------------------------------------------------------------------

@@ -842,6 +842,10 @@ sg_status sg_tc_dft16(int32_t engine, int64_t count, const void *in, void *out, 
     if (engine < SG_ENGINE_TC_BF16X3 || engine > SG_ENGINE_TC_FP16X3 || count < 256 || count % 256 ||
         count / 256 > 0x7FFFFFFF || !in || !out)
         return SG_ERR_ARG;
+    // complex FP32 elements (8-byte loads and stores); the kernel reads and
+    // writes through restrict pointers, so the two ranges must not overlap
+    const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out, bytes = (uintptr_t)count * 16 * 8;
+    if (((a | b) & 7u) || (a < b + bytes && b < a + bytes)) return SG_ERR_ARG;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = launch_tc_stage(engine, in, out, count, inverse ? 1 : 0, (cudaStream_t)stream);

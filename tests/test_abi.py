@@ -101,6 +101,25 @@ def test_null_arguments(lib):
     assert lib.sg_batch_last_error(None) == b""
 
 
+def test_tc_dft16_argument_checks(lib):
+    """The single-stage tensor-core entry point rejects a non-tcgen05 engine,
+    a count that is not a positive multiple of 256, NULL, misaligned and
+    overlapping buffers before any CUDA call (the pointers are never
+    dereferenced)."""
+    tc = N.ENGINES["tc_bf16x3"]
+    a, b = ctypes.c_void_p(0x10000000), ctypes.c_void_p(0x20000000)
+    span = 256 * 16 * 8
+    assert lib.sg_tc_dft16(N.ENGINES["fft32"], 256, a, b, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, 255, a, b, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, -256, a, b, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, 256, None, b, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, 256, ctypes.c_void_p(0x10000004), b, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, 256, a, ctypes.c_void_p(0x20000004), 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, 256, a, a, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, 256, a, ctypes.c_void_p(0x10000000 + span - 8), 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(tc, 256, ctypes.c_void_p(0x10000000 + span - 8), a, 0, None) == N.SG_ERR_ARG
+
+
 def test_status_strings(lib):
     for s in range(8):
         assert lib.sg_status_string(s)

@@ -188,3 +188,12 @@ def test_tcgen05_single_stage_argument_checks():
     assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 100, p, p, 0, None) == N.SG_ERR_ARG
     assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 0, p, p, 0, None) == N.SG_ERR_ARG
     assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 256, None, p, 0, None) == N.SG_ERR_ARG
+    # misaligned or overlapping device buffers are refused, not launched
+    out = torch.empty(256 * 16 * 2, device="cuda:0")
+    q = ctypes.c_void_p(out.data_ptr())
+    assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 256, p, p, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 256, ctypes.c_void_p(buf.data_ptr() + 4), q, 0,
+                           None) == N.SG_ERR_ARG
+    src = torch.randn(256 * 16 * 2, device="cuda:0")
+    assert lib.sg_tc_dft16(N.ENGINES["tc_bf16x3"], 256, ctypes.c_void_p(src.data_ptr()), q, 0, None) == N.SG_OK
+    torch.cuda.synchronize()
