@@ -452,7 +452,9 @@ sg_status sg_tc_dft16(int32_t engine, int64_t count, const void *in, void *out, 
  * op(A) = A ([M][K], leading dim lda) or, with trans_a, A^T (A stored [K][M]);
  * B [K][N] (ldb); C [M][N] (ldc) float and/or C_bf16 (same layout, bf16);
  * stride_* are batch strides in elements (0 broadcasts); bias float [N] or
- * NULL; beta != 0 needs C.  batch <= 65535, N <= 65535 x 128.
+ * NULL; beta != 0 needs C.  batch <= 65535, N <= 65535 x 128.  lda >= K
+ * (M with trans_a), ldb >= N, ldc >= N, strides >= 0, and every pointer
+ * aligned to its element (bf16 2 bytes, float 4), else SG_ERR_ARG.
  * Engine (sg_nn_set_gemm_engine, process-wide, read at each call; set it
  * before calls are issued from several host threads): SG_NN_GEMM_TCGEN05 (default)
  * runs 128 x {32, 64, 128} tiles of tcgen05.mma with the accumulator in

@@ -511,6 +511,12 @@ extern "C" sg_status sg_nn_gemm(int32_t batch, int32_t M, int32_t N, int32_t K, 
     if (batch < 1 || M < 1 || N < 1 || K < 1 || !A || !B || (!C && !C_bf16)) return SG_ERR_ARG;
     if (batch > 65535) return SG_ERR_UNSUPPORTED;
     if (!C && beta != 0.f) return SG_ERR_ARG;
+    // rows at least as long as the operands' (op(A) is M x K); elements
+    // naturally aligned (bf16 2 bytes, float 4 bytes)
+    if (lda < (trans_a ? M : K) || ldb < N || ldc < N || stride_a < 0 || stride_b < 0 || stride_c < 0)
+        return SG_ERR_ARG;
+    if ((((uintptr_t)A | (uintptr_t)B | (uintptr_t)C_bf16) & 1u) || (((uintptr_t)C | (uintptr_t)bias) & 3u))
+        return SG_ERR_ARG;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     cudaStream_t s = (cudaStream_t)stream;
     auto a = (const __nv_bfloat16 *)A;

@@ -120,6 +120,30 @@ def test_tc_dft16_argument_checks(lib):
     assert lib.sg_tc_dft16(tc, 256, ctypes.c_void_p(0x10000000 + span - 8), a, 0, None) == N.SG_ERR_ARG
 
 
+def test_nn_gemm_argument_checks(lib):
+    """sg_nn_gemm refuses short leading dimensions, negative strides and
+    pointers not aligned to their element before any CUDA call."""
+    a, b, c = ctypes.c_void_p(0x10000000), ctypes.c_void_p(0x20000000), ctypes.c_void_p(0x30000000)
+    M, Nn, K = 64, 32, 48
+
+    def call(A=a, lda=K, sa=0, ta=0, B=b, ldb=Nn, sb=0, beta=0.0, C=c, ldc=Nn, sc=0, Cb=None, bias=None):
+        return lib.sg_nn_gemm(2, M, Nn, K, 1.0, A, lda, sa, ta, B, ldb, sb, beta, C, ldc, sc, Cb, bias, None)
+
+    assert call(lda=K - 1) == N.SG_ERR_ARG
+    assert call(ta=1, lda=M - 1) == N.SG_ERR_ARG
+    assert call(ldb=Nn - 1) == N.SG_ERR_ARG
+    assert call(ldc=Nn - 1) == N.SG_ERR_ARG
+    assert call(sa=-1) == N.SG_ERR_ARG
+    assert call(sb=-1) == N.SG_ERR_ARG
+    assert call(sc=-1) == N.SG_ERR_ARG
+    assert call(A=ctypes.c_void_p(0x10000001)) == N.SG_ERR_ARG
+    assert call(B=ctypes.c_void_p(0x20000001)) == N.SG_ERR_ARG
+    assert call(C=ctypes.c_void_p(0x30000002)) == N.SG_ERR_ARG
+    assert call(C=None, Cb=ctypes.c_void_p(0x30000001)) == N.SG_ERR_ARG
+    assert call(bias=ctypes.c_void_p(0x40000002)) == N.SG_ERR_ARG
+    assert call(C=None, beta=1.0, Cb=c) == N.SG_ERR_ARG
+
+
 def test_status_strings(lib):
     for s in range(8):
         assert lib.sg_status_string(s)
