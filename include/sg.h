@@ -442,8 +442,10 @@ sg_status sg_tc_dft16(int32_t engine, int64_t count, const void *in, void *out, 
  * neural operator from them, trains it on fields the FFT solve labels and
  * gates it against that exact path).  Every pointer is a caller-owned
  * device buffer, row-major; "bf16" buffers hold bfloat16, the others float.
- * Each call enqueues on `stream` and returns SG_ERR_ARG for NULL or
- * non-positive sizes, SG_ERR_CUDA for a launch error.
+ * Each call enqueues on `stream` and returns SG_ERR_ARG for NULL,
+ * non-positive sizes, a pointer not aligned to its element (float 4 bytes,
+ * bf16 2, complex float2 8) or an element count beyond 2^31 - 1 where the
+ * kernels index with int, SG_ERR_CUDA for a launch error.
  * ---------------------------------------------------------------------- */
 
 /* Batched GEMM on the tensor cores (bf16 in, FP32 accumulate): for

@@ -792,11 +792,19 @@ int blocks_for(long long n) { return (int)((n + 255) / 256 < 4096 ? (n + 255) / 
 
 }  // namespace
 
+namespace {
+// element pointers aligned to their type (NULL passes); element counts the
+// kernels index with int
+inline bool al(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+inline bool fits(long long n) { return n > 0 && n <= 0x7FFFFFFFLL; }
+}  // namespace
+
 extern "C" {
 
 sg_status sg_nn_spec_combine(int32_t B, int32_t K1, int32_t M1, int32_t C, const float *T, void *V2, void *stream)
 {
     if (!T || !V2 || B < 1 || K1 < 1 || M1 < 1 || C < 1) return SG_ERR_ARG;
+    if (!al(T, 4) || !al(V2, 8) || !fits((long long)B * K1 * M1 * C)) return SG_ERR_ARG;
     const int n = B * K1 * M1 * C;
     k_spec_combine<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, K1, M1, C, T, (float2 *)V2);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
@@ -806,6 +814,7 @@ sg_status sg_nn_spec_combine_bwd(int32_t B, int32_t K1, int32_t M1, int32_t C, c
                                  void *stream)
 {
     if (!dV2 || !dT_bf16 || B < 1 || K1 < 1 || M1 < 1 || C < 1) return SG_ERR_ARG;
+    if (!al(dV2, 8) || !al(dT_bf16, 2) || !fits((long long)B * K1 * M1 * C)) return SG_ERR_ARG;
     const int n = B * K1 * M1 * C;
     k_spec_combine_bwd<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, K1, M1, C, (const float2 *)dV2,
                                                                         (__nv_bfloat16 *)dT_bf16);
@@ -816,6 +825,9 @@ sg_status sg_nn_modemix(int32_t B, int32_t K1, int32_t M1, int32_t C, const void
                         void *stream)
 {
     if (!V2 || !W || !O_bf16 || B < 1 || K1 < 1 || M1 < 1 || C < 1) return SG_ERR_ARG;
+    if (!al(V2, 8) || !al(W, 8) || !al(O_bf16, 2) || !fits((long long)B * K1 * M1 * C) ||
+        !fits((long long)K1 * M1 * C * C))
+        return SG_ERR_ARG;
     const int n = B * K1 * M1 * C;
     k_modemix<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(B, K1, M1, C, (const float2 *)V2, (const float2 *)W,
                                                                (__nv_bfloat16 *)O_bf16);
@@ -826,6 +838,9 @@ sg_status sg_nn_modemix_bwd(int32_t B, int32_t K1, int32_t M1, int32_t C, const 
                             const float *dO, void *dV2, void *dW, void *stream)
 {
     if (!V2 || !W || !dO || (!dV2 && !dW) || B < 1 || K1 < 1 || M1 < 1 || C < 1) return SG_ERR_ARG;
+    if (!al(V2, 8) || !al(W, 8) || !al(dO, 4) || !al(dV2, 8) || !al(dW, 8) || !fits((long long)B * K1 * M1 * C) ||
+        !fits((long long)K1 * M1 * C * C))
+        return SG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (dV2) {
         const int n = B * K1 * M1 * C;
@@ -841,6 +856,7 @@ sg_status sg_nn_modemix_bwd(int32_t B, int32_t K1, int32_t M1, int32_t C, const 
 sg_status sg_nn_act(int64_t n, const float *x, void *y_bf16, int32_t gelu_on, void *stream)
 {
     if (!x || !y_bf16 || n < 1) return SG_ERR_ARG;
+    if (!al(x, 4) || !al(y_bf16, 2)) return SG_ERR_ARG;
     k_act<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, x, (__nv_bfloat16 *)y_bf16, gelu_on);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
@@ -849,6 +865,7 @@ sg_status sg_nn_act_bwd(int64_t n, const float *pre, const float *dy, float *dpr
                         void *stream)
 {
     if (!pre || !dy || (!dpre && !dpre_bf16) || n < 1) return SG_ERR_ARG;
+    if (!al(pre, 4) || !al(dy, 4) || !al(dpre, 4) || !al(dpre_bf16, 2)) return SG_ERR_ARG;
     k_act_bwd<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, pre, dy, dpre, (__nv_bfloat16 *)dpre_bf16, gelu_on);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
@@ -856,6 +873,7 @@ sg_status sg_nn_act_bwd(int64_t n, const float *pre, const float *dy, float *dpr
 sg_status sg_nn_colsum(int64_t rows, int32_t C, const float *x, float *out, int32_t accumulate, void *stream)
 {
     if (!x || !out || rows < 1 || C < 1) return SG_ERR_ARG;
+    if (!al(x, 4) || !al(out, 4)) return SG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (!accumulate) cudaMemsetAsync(out, 0, sizeof(float) * C, s);
     // enough row chunks to fill the GPU (about 2048 blocks), at least 4096 rows each
@@ -872,6 +890,7 @@ sg_status sg_nn_rel_l2(int32_t B, int64_t npix, int32_t CH, const float *pred, c
                        float *dpred, void *stream)
 {
     if (!pred || !tgt || !stats || B < 1 || npix < 1 || CH < 1 || CH > 8) return SG_ERR_ARG;
+    if (!al(pred, 4) || !al(tgt, 4) || !al(stats, 4) || !al(dpred, 4)) return SG_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(stats, 0, sizeof(float) * 2 * B * CH, s);
     dim3 grid(256, B);
@@ -884,6 +903,7 @@ sg_status sg_nn_adam(int64_t n, float *w, const float *g, float *m, float *v, fl
                      int32_t step, void *w_bf16, void *stream)
 {
     if (!w || !g || !m || !v || n < 1 || step < 1) return SG_ERR_ARG;
+    if (!al(w, 4) || !al(g, 4) || !al(m, 4) || !al(v, 4) || !al(w_bf16, 2)) return SG_ERR_ARG;
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     k_adam<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, w, g, m, v, lr, b1, b2, eps, c1, c2,
                                                             (__nv_bfloat16 *)w_bf16);
@@ -893,6 +913,7 @@ sg_status sg_nn_adam(int64_t n, float *w, const float *g, float *m, float *v, fl
 sg_status sg_nn_cast(int64_t n, const float *x, void *y_bf16, void *stream)
 {
     if (!x || !y_bf16 || n < 1) return SG_ERR_ARG;
+    if (!al(x, 4) || !al(y_bf16, 2)) return SG_ERR_ARG;
     k_cast<<<blocks_for(n), 256, 0, (cudaStream_t)stream>>>(n, x, (__nv_bfloat16 *)y_bf16);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
@@ -964,6 +985,7 @@ extern "C" sg_status sg_nn_fields(int32_t B, int32_t nr, int32_t nphi, const flo
                                   float *sigma_d, void *stream)
 {
     if (B < 1 || nr < 1 || nphi < 1 || !params || !sigma_g) return SG_ERR_ARG;
+    if (B > 65535 || !al(params, 4) || !al(sigma_g, 4) || !al(sigma_d, 4)) return SG_ERR_ARG;
     dim3 grid(256, B);
     k_fields<<<grid, 256, 0, (cudaStream_t)stream>>>(nr, nphi, params, sigma_g, sigma_d);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
@@ -982,6 +1004,7 @@ __global__ void k_transpose(int rows, int cols, const float *__restrict__ x, __n
 extern "C" sg_status sg_nn_transpose(int32_t rows, int32_t cols, const float *x, void *y_bf16, void *stream)
 {
     if (rows < 1 || cols < 1 || !x || !y_bf16) return SG_ERR_ARG;
+    if (!al(x, 4) || !al(y_bf16, 2) || !fits((long long)rows * cols)) return SG_ERR_ARG;
     const int n = rows * cols;
     k_transpose<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(rows, cols, x, (__nv_bfloat16 *)y_bf16);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
@@ -1039,6 +1062,7 @@ sg_status sg_nn_pack_inputs(int32_t B, int32_t nr, int32_t nphi, const float *si
                             const float *per_sample, void *x_bf16, void *stream)
 {
     if (B < 1 || nr < 1 || nphi < 1 || !sigma_g || !per_sample || !x_bf16) return SG_ERR_ARG;
+    if (!al(sigma_g, 4) || !al(sigma_d, 4) || !al(per_sample, 4) || !al(x_bf16, 2)) return SG_ERR_ARG;
     k_pack_in<<<1024, 256, 0, (cudaStream_t)stream>>>(B, nr, nphi, sigma_g, sigma_d, per_sample, 0.f,
                                                      (__nv_bfloat16 *)x_bf16);
     return cudaGetLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
@@ -1047,6 +1071,7 @@ sg_status sg_nn_pack_targets(int32_t B, int64_t npix, const float *a, const floa
                              int32_t unpack, void *stream)
 {
     if (B < 1 || npix < 1 || !a || !c || !scale || !t) return SG_ERR_ARG;
+    if (!al(a, 4) || !al(c, 4) || !al(scale, 4) || !al(t, 4)) return SG_ERR_ARG;
     if (unpack)
         k_unpack_out<<<1024, 256, 0, (cudaStream_t)stream>>>(B, npix, t, scale, (float *)a, (float *)c);
     else

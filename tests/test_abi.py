@@ -144,6 +144,26 @@ def test_nn_gemm_argument_checks(lib):
     assert call(C=None, beta=1.0, Cb=c) == N.SG_ERR_ARG
 
 
+def test_nn_pieces_refuse_misaligned_pointers(lib):
+    """The surrogate's elementwise and spectral entry points refuse pointers
+    not aligned to their element and int-overflowing counts before any CUDA
+    call."""
+    f4, odd = ctypes.c_void_p(0x10000000), ctypes.c_void_p(0x10000002)
+    c8 = ctypes.c_void_p(0x20000000)
+    assert lib.sg_nn_spec_combine(2, 4, 4, 8, f4, odd, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_spec_combine(2, 4, 4, 8, odd, c8, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_spec_combine(65536, 1024, 64, 64, f4, c8, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_spec_combine_bwd(2, 4, 4, 8, ctypes.c_void_p(0x20000004), f4, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_modemix(2, 4, 4, 8, c8, ctypes.c_void_p(0x20000004), f4, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_modemix_bwd(2, 4, 4, 8, c8, c8, odd, c8, None, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_act(16, odd, f4, 1, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_act(16, f4, ctypes.c_void_p(0x10000001), 1, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_cast(16, odd, f4, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_colsum(4, 4, f4, odd, 0, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_transpose(65536, 65536, f4, f4, None) == N.SG_ERR_ARG
+    assert lib.sg_nn_pack_targets(1, 16, f4, f4, f4, odd, 0, None) == N.SG_ERR_ARG
+
+
 def test_status_strings(lib):
     for s in range(8):
         assert lib.sg_status_string(s)
