@@ -1061,7 +1061,10 @@ sg_status tune_tiles(sg_batch *b, cudaStream_t s, int reps)
                         bt = t;
                     }
                 }
-        if (st != SG_OK) break;
+        if (st != SG_OK) {
+            sg_set_tiles(pl, &t0);   // the plan keeps its own tiles when a trial fails
+            break;
+        }
         for (size_t i = first; i < b->tile_trials.size(); ++i) {
             const sg_tiles &t = b->tile_trials[i].tiles;
             b->tile_trials[i].chosen = t.rows_fwd == bt.rows_fwd && t.rows_inv == bt.rows_inv &&
