@@ -172,6 +172,11 @@ __device__ __forceinline__ void tma_store_2d(const void *tmap, int x, int y, con
                  "r"(x), "r"(y), "r"(smem_u32(src)), "l"(pol)
                  : "memory");
 }
+// L2 prefetch hint for a contiguous range (16-byte aligned, multiple of 16 bytes)
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Until every committed bulk store has finished reading shared memory.
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }

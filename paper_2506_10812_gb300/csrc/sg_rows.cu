@@ -8,6 +8,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <type_traits>
 #include <utility>
@@ -130,7 +131,7 @@ template <int NC, int NR>
 __global__ void __launch_bounds__(rows_tma_threads(NC, NR), rows_tma_min_blocks(NC, NR, 1024))
 k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const __grid_constant__ CUtensorMap tm,
                const float2 *__restrict__ tw, const float2 *__restrict__ twp, const float *__restrict__ rscale,
-               int dc, unsigned int *tflag, int row0)
+               int dc, unsigned int *tflag, int row0, int ahead)
 {
     static_assert(NR == 2 || NR == 4, "the tensor-copy row transforms take 2 or 4 rows per CTA");
     constexpr int N = NC, T = N / 16, NW = NR * T / 32, PLS = row_pitch_tma(N, NR), XS = T + T / 16;
@@ -163,6 +164,10 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
             for (int r = 0; r < NR; ++r) tma_load_1d(reg + r * IPS, xa + (size_t)(i0 + r) * 2 * N, N * 8, bar, pf);
         }
         if (!__syncthreads_and(mbar_wait_bounded(bar, 0, tflag))) return;
+        // the CTA `ahead` places on (one round of resident CTAs later): its input rows
+        // go to L2 while this round transforms, so the next round does not start on DRAM
+        if (threadIdx.x == 0 && ahead > 0 && blockIdx.x + ahead < gridDim.x)
+            prefetch_l2_bulk(xa + (size_t)(i0 + ahead * NR) * 2 * N, (unsigned)(N * 8 * NR));
         const float2 *xs = reg + g * IPS + t;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {                    // z[n] = x[2n] + i x[2n+1]
@@ -222,6 +227,31 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
         bulk_commit();
         bulk_wait_read_all();
     }
+}
+
+// CTAs of a tensor-copy forward instance resident at once on the current
+// device (CTAs per SM x SMs), queried once per device, row length and rows
+// per CTA; 0 when the query fails (no prefetch then).  The forward rows of
+// the 2048 x 4096 disc run 512 CTAs in two rounds of 304: each first-round
+// CTA prefetches the input rows of the CTA that takes its place, 25.6 against
+// 26.7 us (step 132.0 against 133.4 us).
+template <int NC, int NR> int fwd_resident_ctas()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    int per = 0, nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rows_fwd_tma<NC, NR>, rows_tma_threads(NC, NR),
+                                                      row_tma_smem_bytes(NC, NR)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    v = per * nsm;
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 // ------------------------------------------------------------ row R2C
@@ -346,21 +376,21 @@ cudaError_t launch_rows_fwd(const R *x0, const R *x1, int nsrc, void *xh, int nr
         // whole tiles, each starting on a 16-byte boundary of the map's rows
         if (tm && aligned && rows_tma_eligible(nrows, nphi, false) && nrows_run % NR == 0 && row0 % NR == 0) {
             const dim3 gt(nrows_run / NR, nsrc);
-            auto go = [&](auto kern, int N) {
+            auto go = [&](auto kern, int N, int ahead) {
                 kern<<<gt, NR * N / 16, row_tma_smem_bytes(N, NR), s>>>(x0, x1, *tm, (const float2 *)tw_row,
                                                                         (const float2 *)twp_row, rscale, dc ? 1 : 0,
-                                                                        tflag, row0);
+                                                                        tflag, row0, ahead);
             };
             if (NR == 2) {
-                if (nphi == 4096) go(k_rows_fwd_tma<2048, 2>, 2048);
-                else if (nphi == 2048) go(k_rows_fwd_tma<1024, 2>, 1024);
-                else if (nphi == 1024) go(k_rows_fwd_tma<512, 2>, 512);
-                else go(k_rows_fwd_tma<256, 2>, 256);
+                if (nphi == 4096) go(k_rows_fwd_tma<2048, 2>, 2048, fwd_resident_ctas<2048, 2>());
+                else if (nphi == 2048) go(k_rows_fwd_tma<1024, 2>, 1024, fwd_resident_ctas<1024, 2>());
+                else if (nphi == 1024) go(k_rows_fwd_tma<512, 2>, 512, fwd_resident_ctas<512, 2>());
+                else go(k_rows_fwd_tma<256, 2>, 256, fwd_resident_ctas<256, 2>());
             } else {
-                if (nphi == 4096) go(k_rows_fwd_tma<2048, 4>, 2048);
-                else if (nphi == 2048) go(k_rows_fwd_tma<1024, 4>, 1024);
-                else if (nphi == 1024) go(k_rows_fwd_tma<512, 4>, 512);
-                else go(k_rows_fwd_tma<256, 4>, 256);
+                if (nphi == 4096) go(k_rows_fwd_tma<2048, 4>, 2048, fwd_resident_ctas<2048, 4>());
+                else if (nphi == 2048) go(k_rows_fwd_tma<1024, 4>, 1024, fwd_resident_ctas<1024, 4>());
+                else if (nphi == 1024) go(k_rows_fwd_tma<512, 4>, 512, fwd_resident_ctas<512, 4>());
+                else go(k_rows_fwd_tma<256, 4>, 256, fwd_resident_ctas<256, 4>());
             }
             return cudaGetLastError();
         }
