@@ -228,6 +228,24 @@ def test_lognormal_full_size(nr, nphi):
         assert np.abs(ref[k].ravel()[idx] - samp[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
 
 
+def test_maximum_grid_4096x8192():
+    """The largest grid the FFT method takes (n_r = 4096, n_phi = 8192, 33.5 M
+    cells; both transforms on their runtime-length kernels): the whole field
+    against the FP64 FFT oracle, and the corners and a middle cell against
+    the direct-sum definition."""
+    nr, nphi = 4096, 8192
+    d = rounded(inputs.lognormal_gas(nr, nphi), torch.float32)
+    out = gpu_solve(d)
+    g = grid(d)
+    ref = oracle.fft64(g, d.sigma_g, h_g=d.h_g, G=d.G)
+    assert_close(out, ref, TOL32, f"{nr}x{nphi}")
+    idx = np.array([0, nr * nphi - 1, (nr // 2) * nphi + 17])
+    samp = oracle.direct(g, d.sigma_g, h_g=d.h_g, G=d.G, targets=idx)
+    for k in ("phi_g", "gr_g", "gphi_g"):
+        assert np.abs(out[k].ravel()[idx] - samp[k]).max() <= TOL32[1] * np.abs(ref[k]).max(), k
+        assert np.abs(ref[k].ravel()[idx] - samp[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
+
+
 @pytest.mark.parametrize("nr,nphi,St", [(512, 1024, 1.0), (1024, 2048, 0.1), (2048, 4096, 0.1)])
 def test_lognormal_bifluid_large(nr, nphi, St):
     d = rounded(inputs.lognormal_bifluid(nr, nphi, St=St), torch.float32)
