@@ -79,7 +79,10 @@ enum { SG_COMP_PHI = 0, SG_COMP_R = 1, SG_COMP_AZ = 2 };
 
 typedef struct {
     int32_t nr, nphi;        /* cells.  FFT and SEMISPECTRAL: powers of two,
-                                8 <= nr <= 4096, 32 <= nphi <= 8192.
+                                8 <= nr <= 4096, 32 <= nphi <= 8192; FP64 FFT
+                                plans stage a column's three kernel spectra in
+                                shared memory, so nr <= 2048 gas-only and
+                                nr <= 1024 gas + dust (SG_ERR_UNSUPPORTED above).
                                 DIRECT: nr >= 1, nphi >= 1                          */
     double r_in, r_out;      /* radial cell edges, 0 < r_in < r_out                 */
     double h_g, h_d;         /* aspect ratios H^sg/r of gas and dust (> 0);

@@ -228,22 +228,37 @@ def test_lognormal_full_size(nr, nphi):
         assert np.abs(ref[k].ravel()[idx] - samp[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
 
 
-def test_maximum_grid_4096x8192():
-    """The largest grid the FFT method takes (n_r = 4096, n_phi = 8192, 33.5 M
-    cells; both transforms on their runtime-length kernels): the whole field
+@pytest.mark.parametrize("nr,nphi,dtype,tol", [(4096, 8192, torch.float32, TOL32),
+                                                (2048, 8192, torch.float64, TOL64)])
+def test_maximum_grid(nr, nphi, dtype, tol):
+    """The largest grid the FFT method takes in each dtype (FP32 4096 x 8192,
+    33.5 M cells, both transforms on their runtime-length kernels; FP64
+    2048 x 8192, where its column pass's shared memory ends): the whole field
     against the FP64 FFT oracle, and the corners and a middle cell against
     the direct-sum definition."""
-    nr, nphi = 4096, 8192
-    d = rounded(inputs.lognormal_gas(nr, nphi), torch.float32)
-    out = gpu_solve(d)
+    d = rounded(inputs.lognormal_gas(nr, nphi), dtype)
+    out = gpu_solve(d, dtype)
     g = grid(d)
     ref = oracle.fft64(g, d.sigma_g, h_g=d.h_g, G=d.G)
-    assert_close(out, ref, TOL32, f"{nr}x{nphi}")
+    assert_close(out, ref, tol, f"{nr}x{nphi} {dtype}")
     idx = np.array([0, nr * nphi - 1, (nr // 2) * nphi + 17])
     samp = oracle.direct(g, d.sigma_g, h_g=d.h_g, G=d.G, targets=idx)
     for k in ("phi_g", "gr_g", "gphi_g"):
-        assert np.abs(out[k].ravel()[idx] - samp[k]).max() <= TOL32[1] * np.abs(ref[k]).max(), k
+        assert np.abs(out[k].ravel()[idx] - samp[k]).max() <= tol[1] * np.abs(ref[k]).max(), k
         assert np.abs(ref[k].ravel()[idx] - samp[k]).max() <= 1e-10 * np.abs(ref[k]).max(), k
+
+
+def test_fp64_size_limits_are_refused():
+    """FP64 FFT plans past their shared-memory limit (gas n_r > 2048, gas +
+    dust n_r > 1024) are refused at create with SG_ERR_UNSUPPORTED; FP32
+    takes the same grids."""
+    dev = torch.device("cuda:0")
+    for nr, h_d in ((4096, 0.0), (2048, 0.01)):
+        with pytest.raises(N.SgError) as e:
+            P()(nr, 64, 0.1, 5.0, 0.05, h_d, dtype=torch.float64, device=dev)
+        assert e.value.status == N.SG_ERR_UNSUPPORTED
+        with P()(nr, 64, 0.1, 5.0, 0.05, h_d, dtype=torch.float32, device=dev):
+            pass
 
 
 @pytest.mark.parametrize("nr,nphi,St", [(512, 1024, 1.0), (1024, 2048, 0.1), (2048, 4096, 0.1)])

@@ -175,3 +175,21 @@ def test_entry_points_and_checks():
         with pytest.raises(N.SgError) as e:
             Batch([pl], [sg], [sd], [outs])
         assert e.value.status == N.SG_ERR_ARG
+
+
+def test_flaring_gas_1024x2048_sampled_targets():
+    """The workload bench.py --semi times: FP32 gas at 1024 x 2048 with
+    H = 0.05 r^1.25 (25.8 GB of mode tables), 64 seeded targets plus the
+    grid's corners against the oracle's direct sum with the same H field."""
+    d = inputs.lognormal_gas(1024, 2048, offset=2)
+    d.sigma_g = rounded(d.sigma_g, torch.float32)
+    Hg, _ = flaring(d, 0.25)
+    Hg = rounded(Hg, torch.float32)
+    rng = np.random.default_rng(47)
+    idx = set(rng.choice(d.nr * d.nphi, 64, replace=False).tolist())
+    idx.update([0, d.nphi - 1, (d.nr - 1) * d.nphi, d.nr * d.nphi - 1])
+    idx = np.array(sorted(idx), dtype=np.int64)
+    ref = oracle.direct(grid(d), d.sigma_g, H_g=Hg, G=d.G, targets=idx)
+    with plan_of(d, torch.float32, "semispectral", Hg) as pl:
+        out = solve(pl, d, torch.float32)
+    assert_close({k: v.ravel()[idx] for k, v in out.items()}, ref, TOL32, "semi 1024x2048")
