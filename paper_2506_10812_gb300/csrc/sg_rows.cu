@@ -164,8 +164,8 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
             for (int r = 0; r < NR; ++r) tma_load_1d(reg + r * IPS, xa + (size_t)(i0 + r) * 2 * N, N * 8, bar, pf);
         }
         if (!__syncthreads_and(mbar_wait_bounded(bar, 0, tflag))) return;
-        // the CTA `ahead` places on (one round of resident CTAs later): its input rows
-        // go to L2 while this round transforms, so the next round does not start on DRAM
+        // the CTA `ahead` places on (one wave of resident CTAs later): its input rows
+        // go to L2 while this wave transforms, so the next wave does not start on DRAM
         if (threadIdx.x == 0 && ahead > 0 && blockIdx.x + ahead < gridDim.x)
             prefetch_l2_bulk(xa + (size_t)(i0 + ahead * NR) * 2 * N, (unsigned)(N * 8 * NR));
         const float2 *xs = reg + g * IPS + t;
@@ -232,7 +232,7 @@ k_rows_fwd_tma(const float *__restrict__ x0, const float *__restrict__ x1, const
 // CTAs of a tensor-copy forward instance resident at once on the current
 // device (CTAs per SM x SMs), queried once per device, row length and rows
 // per CTA; 0 when the query fails (no prefetch then).  The forward rows of
-// the 2048 x 4096 disc run 512 CTAs in two rounds of 304: each first-round
+// the 2048 x 4096 disc run 512 CTAs in two waves of 304: each first-wave
 // CTA prefetches the input rows of the CTA that takes its place, 25.6 against
 // 26.7 us (step 132.0 against 133.4 us).
 template <int NC, int NR> int fwd_resident_ctas()
