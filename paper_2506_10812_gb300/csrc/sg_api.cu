@@ -681,7 +681,17 @@ sg_status sg_solve_host(sg_plan *pl, const void *sigma_g, const void *sigma_d, v
     if (!pl->cstream) {
         e = cudaStreamCreateWithFlags(&pl->cstream, cudaStreamNonBlocking);
         for (int i = 0; i < 17 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&pl->cev[i], cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(pl, e, "copy stream");
+        if (e != cudaSuccess) {
+            // leave nothing half made: the next call creates the stream and all its events again
+            for (int i = 0; i < 17; ++i)
+                if (pl->cev[i]) {
+                    cudaEventDestroy(pl->cev[i]);
+                    pl->cev[i] = nullptr;
+                }
+            if (pl->cstream) cudaStreamDestroy(pl->cstream);
+            pl->cstream = nullptr;
+            return cuda_fail(pl, e, "copy stream");
+        }
     }
     char *stg = (char *)pl->stage;
     void *host_out[6] = {phi_g, gr_g, gphi_g, phi_d, gr_d, gphi_d};
