@@ -78,3 +78,29 @@ def test_direct_mode_is_an_option():
     finally:
         sys.argv = argv
     assert args.direct and args.steps == 3 and not args.batch and not args.surrogate
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` runs the FP64 oracle on the host cores on
+    this arm's workload and prints one JSON line of the bench contract: the
+    same metric, unit and config as the main line, its CPU baseline (all
+    cores and one core) and an e2e object without host-device bytes."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["dtype"] == "f64"
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert d["config"]["nr"] == 2048 and d["config"]["nphi"] == 4096 and "2048x4096" in d["config"]["workload"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == os.cpu_count()
+    assert cb["single_core"]["cores"] == 1 and cb["single_core"]["value"] > 0
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
